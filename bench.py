@@ -1,0 +1,268 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 D2Q37 thermal lattice-Boltzmann step, in MLUPS.
+
+Workload: one 4096 x 8192 lattice (33,554,432 fluid sites), periodic in x, thermal
+walls T = 1.15 (bottom) / 0.85 (top), tau = 0.8, g = 1e-4 in -y, Rayleigh-Taylor
+initial state from seed 2 (synthetic; the paper's convective-turbulence workload
+shape).  One bench step = one fused propagate + bc + collide pass over the whole
+lattice (one kernel launch).  Each state buffer is 9.9 GB, far larger than the 129 MB
+L2, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--variant fused|separate]
+    python bench.py --impl reference      # the float64 CPU oracle on a bounded sample
+
+Under torchrun (N > 1) every rank steps its own replica lattice (independent problems:
+weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LX, LY, SEED = 4096, 8192, 2
+TAU, GY, T_BOTTOM, T_TOP = 0.8, -1e-4, 1.15, 0.85
+
+# Algorithmic work per site of the fused FP64 step (counted from the factored
+# formulation in csrc/collide_fp64.cuh; FMA = 2 flops):
+#   138 add + 97 mul + 138 fma + 1 div = 512 flops, 374 FP64-pipe operations.
+FLOPS_PER_SITE_FP64 = 512
+BYTES_PER_SITE_FP64 = 592          # 37 x 8 B read + 37 x 8 B written
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes per launch of the fused FP64 step, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on this workload; None until captured for the current kernel.
+TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--variant", choices=["fused", "separate"], default="fused")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        loaded = [r[0] for r in rows if r[0] > 0.5 * r[1]] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample(steps: int, cols: int = 16):
+    """Time the float64 CPU oracle on a bounded crop of the same workload: ``cols`` full-
+    height columns (cols x 8192 sites) of the seed-2 Rayleigh-Taylor lattice."""
+    import torch
+
+    from oracle import lbm as OL
+    from paper_1703_04594_gb300 import inputs as I
+
+    modes = I.rt_modes(LX, LY, SEED)
+    fields = [t[:cols].contiguous() for t in I.rt_fields(LX, LY, modes, T_BOTTOM, T_TOP, abs(GY))]
+    p = OL.Params(cols, LY, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
+    f = OL.init_equilibrium(*fields)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = OL.step(f, p)
+    dt = time.perf_counter() - t0
+    return {"value": cols * LY * steps / dt / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{cols}x{LY} column crop of the {LX}x{LY} seed-{SEED} RT lattice, {steps} steps, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    oracle_sample(max(1, a.warmup))                    # warm-up steps, untimed
+    cb = oracle_sample(a.steps)
+    line = {"impl": "reference", "metric": "D2Q37 MLUPS", "value": cb["value"], "unit": "MLUPS",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 16 * LY / cb["value"] / 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"D2Q37 FP64 step, {LX}x{LY} RT lattice (oracle on a bounded crop)",
+                       "lx": LX, "ly": LY, "tau": TAU, "gy": GY},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- GPU
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1703_04594_gb300 import inputs as I
+    from paper_1703_04594_gb300 import lbm
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(lbm.LIB_PATH):
+        raise RuntimeError("CUDA library missing: run __graft_entry__.build() first")
+
+    p = lbm.Params(LX, LY, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
+    sites = LX * LY
+    fields = I.rt_state(LX, LY, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))
+    dev = [t.contiguous().cuda() for t in fields]
+    fa, fb = lbm.empty_state(p), lbm.empty_state(p)
+    ftmp = lbm.empty_state(p) if a.variant == "separate" else None
+    lbm.init(p, *dev, fa)
+    stream = torch.cuda.current_stream()
+
+    def one_step(src, dst):
+        if a.variant == "fused":
+            lbm.step(p, src, dst, stream)
+        else:
+            lbm.propagate(p, src, ftmp, stream)
+            lbm.bc(p, src, ftmp, stream)
+            lbm.collide(p, ftmp, dst, stream)
+
+    bufs = [fa, fb]
+    for k in range(a.warmup):
+        one_step(bufs[k % 2], bufs[(k + 1) % 2])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(a.steps):
+            one_step(bufs[(a.warmup + k) % 2], bufs[(a.warmup + k + 1) % 2])
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(a.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+    ms_per_step = total_ms / a.steps
+    value = world * sites * a.steps / (total_ms * 1e-3) / 1e6
+
+    # dominant kernel: the fused step is the only launch of a fused bench step
+    kern_ms = statistics.mean(per_step)
+    achieved = FLOPS_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH[a.variant],
+                "kernel": "k_step_fp64" if a.variant == "fused" else "whole step (3 kernels)",
+                "hbm_gbs_equiv": BYTES_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e9}
+
+    # end to end through the C-ABI from pinned host fields: H2D, init, K steps, moments, D2H
+    pinned_in = [t.contiguous().pin_memory() for t in fields]
+    pinned_out = [torch.empty(LX, LY, dtype=torch.float64).pin_memory() for _ in range(4)]
+    fdev = torch.empty(4 * sites, dtype=torch.float64, device="cuda")
+    del dev
+    lbm.simulate_host(p, pinned_in, 1, pinned_out, fa, fb, fdev, stream)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    lbm.simulate_host(p, pinned_in, a.steps, pinned_out, fa, fb, fdev, stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t)
+    field_bytes = 4 * sites * 8
+    e2e = {"value": world * sites * a.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": field_bytes / a.steps, "d2h_bytes_per_step": field_bytes / a.steps,
+           "what": "lbm_simulate_host: fields H2D + init + K steps + moments + fields D2H, amortised per step"}
+
+    if rank == 0:
+        line = {"metric": "D2Q37 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"D2Q37 FP64 {a.variant} step, {LX}x{LY} Rayleigh-Taylor lattice",
+                           "lx": LX, "ly": LY, "tau": TAU, "gy": GY, "t_bottom": T_BOTTOM, "t_top": T_TOP,
+                           "seed": SEED, "variant": a.variant,
+                           "l2": "state buffers 9.9 GB >> 129 MB L2; no flush needed",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "e2e": e2e,
+                "gpu_launches": a.steps * (1 if a.variant == "fused" else 3),
+                "clocks": clk.summary()}
+        if not a.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = oracle_sample(4)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

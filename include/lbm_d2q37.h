@@ -1,0 +1,140 @@
+/*
+ * lbm_d2q37.h - C ABI of the GB300 (sm_103a) D2Q37 thermal lattice-Boltzmann step.
+ *
+ * Method: arXiv:1703.04594 (Calore, Gabbana, Schifano, Tripiccione), Sec. 3.
+ *   One time step is  propagate -> bc -> collide  (Sec. 5, kernel sequence):
+ *   - propagate (pull form, eq. "master2"): f~_i(x, y) = f_i(x - v_i, t), 37 populations
+ *     hopping up to three sites (Fig. "streamscheme"); x is periodic.
+ *   - bc: thermal walls at y = 0 and y = Ly - 1 act on the three outermost rows (Sec. 5).
+ *     A population pulled from outside the fluid takes the wall equilibrium
+ *     f_i^eq(rho_w, 0, T_wall), rho_w = density at the start of the step of the fluid site
+ *     next to the wall in the source column.
+ *   - collide: BGK relaxation (eq. "lbequation") towards the fourth-order Hermite
+ *     equilibrium of the moments (eq. "macro"), evaluated at the gravity-shifted velocity
+ *     u + tau g and temperature T + tau (1 - tau) |g|^2 / D.
+ *
+ * Units: molecular velocities xi_i = c v_i with integer hops v_i and the lattice scale c
+ * (see lbm_model); velocity, temperature and gravity are in xi units, reference T0 = 1.
+ *
+ * Layout (structure of arrays, Sec. 4, "SoA"; y contiguous, two copies read and written
+ * alternately): population i of site (x, y) is element  i*lx*pitch + x*pitch + y  of a
+ * state buffer.  pitch = lbm_pitch(p) >= ly; elements y >= ly of a column are padding and
+ * are never read.  FP64 states hold double f_i.  FP32_SHIFTED states hold float
+ * (f_i - w_i * rho0).  Population order: 0 = rest, 1..18 = the vectors returned by
+ * lbm_model in that order, 18 + k = -(vector k).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are device pointers; *_host are host pointers.  The caller
+ *     owns every buffer and the stream; no entry point allocates device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *     are stream-ordered and asynchronous unless stated otherwise.
+ *   - Return value: LBM_OK, or an lbm_status error code.  Invalid arguments are
+ *     rejected with LBM_EINVAL before anything is launched.  LBM_ECUDA reports a launch
+ *     or copy failure; lbm_last_cuda_error() returns the CUDA error code.
+ *   - State buffers must be 256-byte aligned (cudaMalloc and torch guarantee it); a
+ *     step's input and output must not overlap (the pull scheme needs two copies).
+ */
+#ifndef LBM_D2Q37_H
+#define LBM_D2Q37_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, LBM_ENOMEM = 4 };
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
+enum lbm_bc { LBM_BC_WALLS = 0, LBM_BC_PERIODIC_Y = 1 /* test mode: y wraps like x */ };
+
+/* Problem parameters, as the paper states the problem (Sec. 3): lattice size, BGK
+ * relaxation time tau (> 0.5), gravity (gx, gy) per time step in xi units, wall
+ * temperatures.  rho0 is the reference density of the FP32_SHIFTED storage.
+ * Constraints: lx >= 4, ly >= 6, lx * ly * 37 < 2^40. */
+typedef struct lbm_params {
+  int32_t lx, ly;
+  int32_t precision; /* enum lbm_precision */
+  int32_t bc;        /* enum lbm_bc */
+  double tau;
+  double gx, gy;
+  double t_bottom, t_top;
+  double rho0;
+} lbm_params;
+
+/* Library ABI version (incremented on any incompatible change). */
+int32_t lbm_version(void);
+
+/* Model constants (host only, no GPU needed): lattice scale c, the 37 weights w_i and
+ * integer hops (vx_i, vy_i) in the library's population order.  Any pointer may be NULL.
+ * Sec. 3 / Fig. "streamscheme" for the 37 hops; the weights and c solve the lattice
+ * isotropy conditions up to eighth order. */
+int32_t lbm_model(double* c, double* w37, int32_t* vx37, int32_t* vy37);
+
+/* Elements per y-column of a state buffer (ly rounded up to 32), or -1 if p is invalid. */
+int64_t lbm_pitch(const lbm_params* p);
+/* Bytes of one state buffer: 37 * lx * pitch * element size, or -1 if p is invalid. */
+int64_t lbm_buffer_bytes(const lbm_params* p);
+
+/* Populations at local equilibrium with the given fields (Sec. 3: an LB run starts from
+ * an assignment of the populations matching the initial condition):
+ * f_i = f_i^eq(rho, (ux, uy), T).  Fields are [lx][ly] doubles, y contiguous. */
+int32_t lbm_init(const lbm_params* p, const double* rho_dev, const double* ux_dev,
+                 const double* uy_dev, const double* T_dev, void* f_dev, void* stream);
+
+/* One fused time step (propagate + bc + collide in a single pull kernel):
+ * f_out = step(f_in).  f_in and f_out must not overlap. */
+int32_t lbm_step(const lbm_params* p, const void* f_in_dev, void* f_out_dev, void* stream);
+
+/* n_steps fused steps, alternating between the two buffers (the paper's two lattice
+ * copies, Sec. 4).  The result is in f_a when n_steps is even, else in f_b. */
+int32_t lbm_run(const lbm_params* p, void* f_a_dev, void* f_b_dev, int32_t n_steps, void* stream);
+
+/* The step as three separate kernels, in the paper's order (Sec. 5):
+ *   lbm_propagate: f_tmp_i(x, y) = f_in_i(x - vx_i, y - vy_i) for every source inside
+ *                  the fluid (entries whose source is outside are left untouched);
+ *   lbm_bc:        writes the wall equilibria into exactly those entries of f_tmp, with
+ *                  rho_w taken from f_in;
+ *   lbm_collide:   f_out = collide(f_tmp), site by site.
+ * propagate -> bc -> collide equals lbm_step up to floating-point contraction order.
+ * FP64 only. */
+int32_t lbm_propagate(const lbm_params* p, const void* f_in_dev, void* f_tmp_dev, void* stream);
+int32_t lbm_bc(const lbm_params* p, const void* f_in_dev, void* f_tmp_dev, void* stream);
+int32_t lbm_collide(const lbm_params* p, const void* f_tmp_dev, void* f_out_dev, void* stream);
+
+/* Macroscopic fields of a state (eq. "macro"): rho = sum f, rho u = sum xi f,
+ * D rho T = sum |xi - u|^2 f.  Outputs are [lx][ly] doubles. */
+int32_t lbm_moments(const lbm_params* p, const void* f_dev, double* rho_dev, double* ux_dev,
+                    double* uy_dev, double* T_dev, void* stream);
+
+/* Bytes of scratch lbm_kinetic_energy needs for this lattice. */
+int64_t lbm_reduce_scratch_bytes(const lbm_params* p);
+
+/* Total kinetic energy sum over fluid sites of rho |u|^2 / 2 (moments of eq. "macro"),
+ * written to *out_dev.  Deterministic: per-block partial sums go to scratch_dev
+ * (>= lbm_reduce_scratch_bytes bytes, device memory owned by the caller) and are then
+ * summed in a fixed order by one block. */
+int32_t lbm_kinetic_energy(const lbm_params* p, const void* f_dev, double* out_dev,
+                           void* scratch_dev, size_t scratch_bytes, void* stream);
+
+/* End-to-end run from host memory (synchronous): copies the four initial fields from
+ * host (pinned for best speed) to fields_dev (4 * lx * ly doubles, device), builds the
+ * equilibrium state in f_a_dev, runs n_steps fused steps between f_a_dev and f_b_dev,
+ * computes the moments into fields_dev and copies them back to the four *_out_host
+ * arrays.  Returns after the last copy has finished. */
+int32_t lbm_simulate_host(const lbm_params* p, const double* rho_host, const double* ux_host,
+                          const double* uy_host, const double* T_host, int32_t n_steps,
+                          double* rho_out_host, double* ux_out_host, double* uy_out_host,
+                          double* T_out_host, void* f_a_dev, void* f_b_dev, double* fields_dev,
+                          void* stream);
+
+/* Human-readable text of an lbm_status code. */
+const char* lbm_strerror(int32_t status);
+/* The CUDA error code behind the most recent LBM_ECUDA on this thread (0 if none). */
+int32_t lbm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_D2Q37_H */

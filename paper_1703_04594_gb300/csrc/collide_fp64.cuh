@@ -1,0 +1,141 @@
+// FP64 collision of one site, factored for the FP64 pipe.
+//
+// Computes the BGK update (Sec. 3, eq. "lbequation", dt = 1)
+//     f_i' = f_i + (f_i^eq - f_i) / tau
+// with the moments of eq. "macro" (xi_i = c v_i):
+//     rho = sum f,  rho u = sum xi f,  D rho T = sum |xi - u|^2 f = c^2 sum |v|^2 f - rho |u|^2,
+// and the fourth-order Hermite equilibrium evaluated at the gravity-shifted
+// u_s = u + tau g, T_s = T + tau (1 - tau) |g|^2 / D.  Written as a polynomial in
+// s = xi_i . u_s with t = T_s - 1, U = |u_s|^2, q = |xi_i|^2 (D = 2):
+//     f_i^eq / (w_i rho) = C0(q) + C1(q) s + C2(q) s^2 + s^3/6 + s^4/24,
+//     C2 = 1/2 - U/4 + t (q - D - 4)/4,   C1 = 1 - U/2 + t (q - D - 2)/2,
+//     C0 = 1 - U/2 + t (q - D)/2 + U^2/8 + t U (D + 2 - q)/4 + t^2 (q^2 - 2(D+2) q + D(D+2))/8.
+// Work saved against the textbook form (Sec. 3 quotes ~7000 flops per site):
+//   * moments are sums over opposite pairs P = f_v + f_-v, M = f_v - f_-v with integer
+//     velocity weights grouped by value;
+//   * C0..C2 are per shell (8 values of q), pre-multiplied by omega w_s rho;
+//   * each opposite pair shares the even part E(s^2) and odd part O(s):
+//     f_v^eq = E + O, f_-v^eq = E - O.
+#pragma once
+#include "d2q37_model.cuh"
+
+namespace d2q37 {
+
+struct CollideConst {
+  double omega;   // 1 / tau
+  double om1;     // 1 - 1 / tau
+  double cgx;     // c * tau * gx   (shift of c * u_x)
+  double cgy;     // c * tau * gy
+  double tshift;  // tau (1 - tau) |g|^2 / D - 1
+};
+
+// Moments in integer-velocity units: rho = sum f, (jx, jy) = sum v f, e = sum |v|^2 f.
+__device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, double& jx, double& jy,
+                                            double& e) {
+  double P[NPAIR + 1], M[NPAIR + 1];
+#pragma unroll
+  for (int k = 1; k <= NPAIR; ++k) {
+    P[k] = f[k] + f[k + NPAIR];
+    M[k] = f[k] - f[k + NPAIR];
+  }
+  // shell sums of the pair sums (shells 1..7 hold |v|^2 = 1, 2, 4, 5, 8, 9, 10)
+  const double S1 = P[1] + P[2], S2 = P[3] + P[4], S3 = P[5] + P[6];
+  const double S4 = (P[7] + P[8]) + (P[9] + P[10]), S5 = P[11] + P[12], S6 = P[13] + P[14];
+  const double S7 = (P[15] + P[16]) + (P[17] + P[18]);
+  rho = ((f[0] + S1) + (S2 + S3)) + ((S4 + S5) + (S6 + S7));
+  e = fma(10.0, S7, fma(9.0, S6, fma(8.0, S5, fma(5.0, S4, fma(4.0, S3, fma(2.0, S2, S1))))));
+  // x: vx = 1 for k in {1,3,4,8,10,16,18}, 2 for {5,7,9,11,12}, 3 for {13,15,17}
+  const double X1 = ((M[1] + M[3]) + (M[4] + M[8])) + ((M[10] + M[16]) + M[18]);
+  const double X2 = (M[5] + M[7]) + (M[9] + M[11]) + M[12];
+  const double X3 = (M[13] + M[15]) + M[17];
+  jx = fma(3.0, X3, fma(2.0, X2, X1));
+  // y: vy = +1 {2,3,7,15}, -1 {4,9,17}, +2 {6,8,11}, -2 {10,12}, +3 {14,16}, -3 {18}
+  const double Y1 = ((M[2] + M[3]) + (M[7] + M[15])) - ((M[4] + M[9]) + M[17]);
+  const double Y2 = (M[6] + M[8]) + M[11] - (M[10] + M[12]);
+  const double Y3 = (M[14] + M[16]) - M[18];
+  jy = fma(3.0, Y3, fma(2.0, Y2, Y1));
+}
+
+// Equilibrium coefficients of one site.  R = omega * rho for a collision (the result is
+// omega f^eq), or rho for a plain equilibrium.  Outputs per shell s = 0..7 the Horner
+// coefficients K0..K4 of R w_s (C0 + C1 s + C2 s^2 + s^3/6 + s^4/24).
+struct ShellCoef {
+  double K0[8], K1[8], K2[8], K3[8], K4[8];
+};
+
+__device__ __forceinline__ void shell_coefficients(double R, double t, double U, ShellCoef& k) {
+  const double tU = t * U, t2 = t * t;
+  const double a00 = fma(0.125, U * U, fma(-0.5, U, 1.0) - t) + (tU + t2);
+  const double a01 = fma(-0.25, tU, 0.5 * t) - t2;
+  const double a02 = 0.125 * t2;
+  const double a10 = fma(-0.5, U, 1.0) - 2.0 * t;
+  const double a11 = 0.5 * t;
+  const double a20 = fma(-0.25, U, 0.5) - 1.5 * t;
+  const double a21 = 0.25 * t;
+  k.K0[0] = (R * w_shell(0)) * a00;
+#pragma unroll
+  for (int s = 1; s < 8; ++s) {
+    const double q = q_shell(s);
+    const double W = R * w_shell(s);
+    k.K0[s] = W * fma(fma(a02, q, a01), q, a00);
+    k.K1[s] = W * fma(a11, q, a10);
+    k.K2[s] = W * fma(a21, q, a20);
+    k.K3[s] = W * (1.0 / 6.0);
+    k.K4[s] = W * (1.0 / 24.0);
+  }
+}
+
+// s = v . (Ux, Uy) for integer v with |vx|, |vy| <= 3, from precomputed multiples.
+struct Multiples {
+  double X[4], Y[4];
+};
+__device__ __forceinline__ Multiples make_multiples(double Ux, double Uy) {
+  Multiples m;
+  m.X[0] = 0.0; m.X[1] = Ux; m.X[2] = Ux + Ux; m.X[3] = m.X[2] + Ux;
+  m.Y[0] = 0.0; m.Y[1] = Uy; m.Y[2] = Uy + Uy; m.Y[3] = m.Y[2] + Uy;
+  return m;
+}
+__device__ __forceinline__ double dot_v(const Multiples& m, int vxk, int vyk) {
+  // vxk >= 0 for representatives
+  if (vyk == 0) return m.X[vxk];
+  if (vxk == 0) return vyk > 0 ? m.Y[vyk] : -m.Y[-vyk];
+  return vyk > 0 ? m.X[vxk] + m.Y[vyk] : m.X[vxk] - m.Y[-vyk];
+}
+
+// Relaxation: out_i = om1 * f_i + R w_i P_i(s_i), for a whole site.  With om1 = 0 and
+// R = rho this is the plain equilibrium.  `store(i, value)` receives each population.
+template <class Store>
+__device__ __forceinline__ void relax_site(const double (&f)[Q], double om1, double R, double Ux, double Uy,
+                                           double t, Store&& store) {
+  const double U = fma(Ux, Ux, Uy * Uy) * (1.0 / C2);
+  ShellCoef k;
+  shell_coefficients(R, t, U, k);
+  const Multiples m = make_multiples(Ux, Uy);
+  store(0, fma(om1, f[0], k.K0[0]));
+#pragma unroll
+  for (int j = 1; j <= NPAIR; ++j) {
+    const int sh = shell(j);
+    const double s = dot_v(m, rep_vx(j), rep_vy(j));
+    const double s2 = s * s;
+    const double E = fma(fma(k.K4[sh], s2, k.K2[sh]), s2, k.K0[sh]);
+    const double O = s * fma(k.K3[sh], s2, k.K1[sh]);
+    store(j, fma(om1, f[j], E + O));
+    store(j + NPAIR, fma(om1, f[j + NPAIR], E - O));
+  }
+}
+
+// Full collision of one site (moments -> gravity shift -> equilibrium -> BGK).
+template <class Store>
+__device__ __forceinline__ void collide_site(const double (&f)[Q], const CollideConst& cc, Store&& store) {
+  double rho, jx, jy, e;
+  moments_int(f, rho, jx, jy, e);
+  const double inv_rho = 1.0 / rho;
+  const double c2ir = C2 * inv_rho;
+  const double Ux0 = jx * c2ir, Uy0 = jy * c2ir;              // c * u
+  const double uu = fma(Ux0, Ux0, Uy0 * Uy0) * (1.0 / C2);     // |u|^2
+  const double TD = fma(e, c2ir, -uu);                         // D T
+  const double t = fma(TD, 1.0 / D, cc.tshift);                // T_s - 1
+  relax_site(f, cc.om1, cc.omega * rho, Ux0 + cc.cgx, Uy0 + cc.cgy, t, store);
+}
+
+}  // namespace d2q37

@@ -1,0 +1,293 @@
+// FP64 kernels: fused pull step, the separate propagate / bc / collide kernels,
+// equilibrium initialisation, moments and the kinetic-energy reduction.
+//
+// Thread mapping (all site kernels): block = 32 x 4 threads; threadIdx.x runs along y
+// (the contiguous axis, Sec. 4 "column-major, Y innermost"), so each warp owns 32
+// consecutive sites of one column x and every population load/store of a warp is one
+// contiguous 256-byte run (shifted by the hop's vy for loads).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "collide_fp64.cuh"
+#include "kernels.h"
+
+namespace d2q37 {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Source column offsets x_s * pitch for hops vx = -3..3 (index vx + 3), x periodic.
+__device__ __forceinline__ void source_columns(int x, const StepArgs& a, long long (&col)[7]) {
+#pragma unroll
+  for (int d = 0; d < 7; ++d) col[d] = (long long)wrap(x - (d - 3), a.lx) * a.pitch;
+}
+
+// Wall densities rho(x_s, 0) and rho(x_s, ly-1) of the seven source columns, computed by
+// lanes 0..6 (bottom) and 8..14 (top) of the warp and broadcast to all lanes.
+// Every lane of the warp must call this (it shuffles with the full mask).
+__device__ __forceinline__ void wall_densities(const double* __restrict__ fin, int x, const StepArgs& a,
+                                               double (&rb)[7], double (&rt)[7]) {
+  const int lane = threadIdx.x & 31;
+  const int d = lane & 7;
+  const int row = lane < 8 ? 0 : a.ly - 1;
+  double r = 0.0;
+  if (d < 7 && lane < 16) {
+    const double* src = fin + (long long)wrap(x - (d - 3), a.lx) * a.pitch + row;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) r += __ldg(src + i * a.pop);
+  }
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    rb[j] = __shfl_sync(FULL, r, j);
+    rt[j] = __shfl_sync(FULL, r, 8 + j);
+  }
+}
+
+// Pull-gather of the 37 populations of site (x, yc) (Sec. 3, eq. "master2"), with the
+// thermal-wall values for sources outside the fluid.  WALL selects the slow path used by
+// warps within three rows of a wall.
+template <bool PERIODIC, bool WALL>
+__device__ __forceinline__ void gather(const double* __restrict__ fin, int yc, const long long (&col)[7],
+                                       const StepArgs& a, const double (&rb)[7], const double (&rt)[7],
+                                       double (&f)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int ys = yc - vy(i);
+    const double* src = fin + i * a.pop + col[vx(i) + 3];
+    if (PERIODIC) {
+      f[i] = __ldg(src + wrap(ys, a.ly));
+    } else if (!WALL) {
+      f[i] = __ldg(src + ys);
+    } else {
+      if (vy(i) > 0 && ys < 0) {
+        f[i] = rb[vx(i) + 3] * a.wall_b[i];
+      } else if (vy(i) < 0 && ys >= a.ly) {
+        f[i] = rt[vx(i) + 3] * a.wall_t[i];
+      } else {
+        f[i] = __ldg(src + ys);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Fused step: gather (propagate + bc) -> collide -> streaming store.
+template <bool PERIODIC>
+__global__ void __launch_bounds__(128) k_step_fp64(const double* __restrict__ fin, double* __restrict__ fout,
+                                                   StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  if (x >= a.lx) return;  // uniform per warp
+  const int y0 = blockIdx.x * 32;
+  const int y = y0 + threadIdx.x;
+  const bool active = y < a.ly;
+  const int yc = active ? y : a.ly - 1;
+  long long col[7];
+  source_columns(x, a, col);
+  double f[Q];
+  double rb[7], rt[7];
+  const bool wall_warp = !PERIODIC && (y0 < 3 || y0 + 32 > a.ly - 3);
+  if (wall_warp) {
+    wall_densities(fin, x, a, rb, rt);
+    gather<PERIODIC, true>(fin, yc, col, a, rb, rt, f);
+  } else {
+    gather<PERIODIC, false>(fin, yc, col, a, rb, rt, f);
+  }
+  if (!active) return;
+  double* dst = fout + (long long)x * a.pitch + y;
+  collide_site(f, a.cc, [&](int i, double v) { __stcs(dst + i * a.pop, v); });
+}
+
+// ---------------------------------------------------------------------------------------
+// Separate kernels (the paper's propagate -> bc -> collide sequence, Sec. 5).
+template <bool PERIODIC>
+__global__ void __launch_bounds__(128) k_propagate_fp64(const double* __restrict__ fin,
+                                                        double* __restrict__ ftmp, StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  long long col[7];
+  source_columns(x, a, col);
+  double* dst = ftmp + (long long)x * a.pitch + y;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int ys = y - vy(i);
+    if (PERIODIC) ys = wrap(ys, a.ly);
+    else if (ys < 0 || ys >= a.ly) continue;  // left for bc
+    __stcs(dst + i * a.pop, __ldg(fin + i * a.pop + col[vx(i) + 3] + ys));
+  }
+}
+
+// One thread per (column x, wall row r in 0..5): rows 0,1,2 and ly-3, ly-2, ly-1.
+__global__ void __launch_bounds__(128) k_bc_fp64(const double* __restrict__ fin, double* __restrict__ ftmp,
+                                                 StepArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.lx * 6) return;
+  const int x = t / 6, r = t % 6;
+  const bool bottom = r < 3;
+  const int y = bottom ? r : a.ly - 6 + r;
+  const int wall_row = bottom ? 0 : a.ly - 1;
+  double* dst = ftmp + (long long)x * a.pitch + y;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int ys = y - vy(i);
+    const bool outside = bottom ? (ys < 0) : (ys >= a.ly);
+    if (!outside) continue;
+    const double* src = fin + (long long)wrap(x - vx(i), a.lx) * a.pitch + wall_row;
+    double rw = 0.0;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) rw += __ldg(src + j * a.pop);
+    dst[i * a.pop] = rw * (bottom ? a.wall_b[i] : a.wall_t[i]);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_collide_fp64(const double* __restrict__ ftmp, double* __restrict__ fout,
+                                                      StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  const long long o = (long long)x * a.pitch + y;
+  double f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = __ldg(ftmp + o + i * a.pop);
+  double* dst = fout + o;
+  collide_site(f, a.cc, [&](int i, double v) { __stcs(dst + i * a.pop, v); });
+}
+
+// ---------------------------------------------------------------------------------------
+// f_i = f_i^eq(rho, u, T) from [lx][ly] fields.
+__global__ void __launch_bounds__(128) k_init_fp64(const double* __restrict__ rho, const double* __restrict__ ux,
+                                                   const double* __restrict__ uy, const double* __restrict__ T,
+                                                   double* __restrict__ fout, StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  const long long fi = (long long)x * a.ly + y;
+  double f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = 0.0;
+  double* dst = fout + (long long)x * a.pitch + y;
+  relax_site(f, 0.0, rho[fi], C * ux[fi], C * uy[fi], T[fi] - 1.0, [&](int i, double v) { dst[i * a.pop] = v; });
+}
+
+__device__ __forceinline__ void site_fields(const double (&f)[Q], double& rho, double& ux, double& uy, double& T) {
+  double jx, jy, e;
+  moments_int(f, rho, jx, jy, e);
+  const double inv_rho = 1.0 / rho;
+  ux = C * jx * inv_rho;
+  uy = C * jy * inv_rho;
+  T = (C2 * e * inv_rho - fma(ux, ux, uy * uy)) / D;
+}
+
+__global__ void __launch_bounds__(128) k_moments_fp64(const double* __restrict__ fin, double* __restrict__ rho,
+                                                      double* __restrict__ ux, double* __restrict__ uy,
+                                                      double* __restrict__ T, StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  const long long o = (long long)x * a.pitch + y;
+  double f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = __ldg(fin + o + i * a.pop);
+  const long long fi = (long long)x * a.ly + y;
+  site_fields(f, rho[fi], ux[fi], uy[fi], T[fi]);
+}
+
+// Kinetic energy: per-block partial sums (fixed order), then one block sums the partials.
+__global__ void __launch_bounds__(128) k_ke_partial_fp64(const double* __restrict__ fin, double* __restrict__ part,
+                                                         StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  double ke = 0.0;
+  if (x < a.lx && y < a.ly) {
+    const long long o = (long long)x * a.pitch + y;
+    double f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = __ldg(fin + o + i * a.pop);
+    double rho, ux, uy, T;
+    site_fields(f, rho, ux, uy, T);
+    ke = 0.5 * rho * fma(ux, ux, uy * uy);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ke += __shfl_down_sync(FULL, ke, off);
+  __shared__ double warp_sum[4];
+  if (threadIdx.x == 0) warp_sum[threadIdx.y] = ke;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0)
+    part[blockIdx.y * gridDim.x + blockIdx.x] = (warp_sum[0] + warp_sum[1]) + (warp_sum[2] + warp_sum[3]);
+}
+
+__global__ void __launch_bounds__(256) k_reduce_sum(const double* __restrict__ part, long long n,
+                                                    double* __restrict__ out) {
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(FULL, s, off);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    *out = t;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launchers.
+static inline dim3 site_grid(const StepArgs& a) { return dim3((a.ly + 31) / 32, (a.lx + 3) / 4); }
+static const dim3 kSiteBlock(32, 4);
+
+cudaError_t launch_step_fp64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s) {
+  if (a.periodic) k_step_fp64<true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+  else k_step_fp64<false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s) {
+  if (a.periodic) k_propagate_fp64<true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, ftmp, a);
+  else k_propagate_fp64<false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, ftmp, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bc_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s) {
+  if (a.periodic) return cudaSuccess;
+  const int n = a.lx * 6;
+  k_bc_fp64<<<(n + 127) / 128, 128, 0, s>>>(fin, ftmp, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collide_fp64(const double* ftmp, double* fout, const StepArgs& a, cudaStream_t s) {
+  k_collide_fp64<<<site_grid(a), kSiteBlock, 0, s>>>(ftmp, fout, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy, const double* T, double* f,
+                             const StepArgs& a, cudaStream_t s) {
+  k_init_fp64<<<site_grid(a), kSiteBlock, 0, s>>>(rho, ux, uy, T, f, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_fp64(const double* f, double* rho, double* ux, double* uy, double* T,
+                                const StepArgs& a, cudaStream_t s) {
+  k_moments_fp64<<<site_grid(a), kSiteBlock, 0, s>>>(f, rho, ux, uy, T, a);
+  return cudaGetLastError();
+}
+
+long long ke_partial_count(const StepArgs& a) {
+  const dim3 g = site_grid(a);
+  return (long long)g.x * g.y;
+}
+
+cudaError_t launch_kinetic_energy_fp64(const double* f, double* out, double* part, const StepArgs& a,
+                                       cudaStream_t s) {
+  k_ke_partial_fp64<<<site_grid(a), kSiteBlock, 0, s>>>(f, part, a);
+  k_reduce_sum<<<1, 256, 0, s>>>(part, ke_partial_count(a), out);
+  return cudaGetLastError();
+}
+
+}  // namespace d2q37

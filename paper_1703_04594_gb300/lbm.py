@@ -1,0 +1,254 @@
+"""Thin Python binding of the C-ABI in ``include/lbm_d2q37.h`` (argument marshalling only).
+
+Every entry point has the same name as its C function without the ``lbm_`` prefix.
+Device buffers are torch CUDA tensors (PyTorch supplies memory and streams only); the
+work itself runs in the library's kernels.  The library is loaded on first use and a
+missing library raises ``RuntimeError``: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_native", "liblbm_d2q37.so")
+
+FP64, FP32_SHIFTED = 0, 1
+BC_WALLS, BC_PERIODIC_Y = 0, 1
+Q = 37
+
+OK, EINVAL, ECUDA, ETIMEOUT, ENOMEM = 0, 1, 2, 3, 4
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("lx", ctypes.c_int32), ("ly", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("bc", ctypes.c_int32), ("tau", ctypes.c_double), ("gx", ctypes.c_double),
+                ("gy", ctypes.c_double), ("t_bottom", ctypes.c_double), ("t_top", ctypes.c_double),
+                ("rho0", ctypes.c_double)]
+
+
+@dataclass(frozen=True)
+class Params:
+    """Problem parameters (Sec. 3): lattice size, relaxation time, gravity (xi units per
+    step), wall temperatures; ``precision`` and ``bc`` select the storage form and the
+    y boundary."""
+    lx: int
+    ly: int
+    tau: float = 0.8
+    gx: float = 0.0
+    gy: float = -1e-4
+    t_bottom: float = 1.15
+    t_top: float = 0.85
+    rho0: float = 1.0
+    precision: int = FP64
+    bc: int = BC_WALLS
+
+    def c(self) -> CParams:
+        return CParams(self.lx, self.ly, self.precision, self.bc, self.tau, self.gx, self.gy,
+                       self.t_bottom, self.t_top, self.rho0)
+
+
+class LbmError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        lib = _lib()
+        msg = lib.lbm_strerror(status).decode()
+        if status == ECUDA:
+            msg += f" (cuda error {lib.lbm_last_cuda_error()})"
+        super().__init__(f"{fn}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+_VP = ctypes.c_void_p
+_PP = ctypes.POINTER(CParams)
+_SIGS = {
+    "lbm_version": (ctypes.c_int32, []),
+    "lbm_model": (ctypes.c_int32, [_VP, _VP, _VP, _VP]),
+    "lbm_pitch": (ctypes.c_int64, [_PP]),
+    "lbm_buffer_bytes": (ctypes.c_int64, [_PP]),
+    "lbm_init": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "lbm_step": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
+    "lbm_run": (ctypes.c_int32, [_PP, _VP, _VP, ctypes.c_int32, _VP]),
+    "lbm_propagate": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
+    "lbm_bc": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
+    "lbm_collide": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
+    "lbm_moments": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "lbm_reduce_scratch_bytes": (ctypes.c_int64, [_PP]),
+    "lbm_kinetic_energy": (ctypes.c_int32, [_PP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "lbm_simulate_host": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
+                                           _VP, _VP, _VP, _VP]),
+    "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
+    "lbm_last_cuda_error": (ctypes.c_int32, []),
+}
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -m paper_1703_04594_gb300.build`)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(fn: str, status: int):
+    if status != OK:
+        raise LbmError(fn, status)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------------- host-only
+def version() -> int:
+    return _lib().lbm_version()
+
+
+def model():
+    """(c, w[37], vx[37], vy[37]) as the library defines them (host only)."""
+    c = ctypes.c_double()
+    w = (ctypes.c_double * Q)()
+    vx = (ctypes.c_int32 * Q)()
+    vy = (ctypes.c_int32 * Q)()
+    _check("lbm_model", _lib().lbm_model(ctypes.byref(c), w, vx, vy))
+    return c.value, list(w), list(vx), list(vy)
+
+
+def pitch(p: Params) -> int:
+    v = _lib().lbm_pitch(ctypes.byref(p.c()))
+    if v < 0:
+        raise LbmError("lbm_pitch", EINVAL)
+    return v
+
+
+def buffer_bytes(p: Params) -> int:
+    v = _lib().lbm_buffer_bytes(ctypes.byref(p.c()))
+    if v < 0:
+        raise LbmError("lbm_buffer_bytes", EINVAL)
+    return v
+
+
+def state_dtype(p: Params):
+    return torch.float64 if p.precision == FP64 else torch.float32
+
+
+def empty_state(p: Params, device="cuda") -> torch.Tensor:
+    """An uninitialised state buffer [37, lx, pitch] of the storage type."""
+    return torch.empty((Q, p.lx, pitch(p)), dtype=state_dtype(p), device=device)
+
+
+def _state(p: Params, t: torch.Tensor, name: str):
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == state_dtype(p)
+            and t.numel() * t.element_size() >= buffer_bytes(p)):
+        raise ValueError(f"{name}: expected a contiguous CUDA {state_dtype(p)} tensor of "
+                         f"{buffer_bytes(p)} bytes, got {t.dtype} {tuple(t.shape)} on {t.device}")
+    return _ptr(t)
+
+
+def _field(p: Params, t: torch.Tensor, name: str):
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.float64 and t.numel() == p.lx * p.ly):
+        raise ValueError(f"{name}: expected a contiguous CUDA float64 [lx, ly] tensor")
+    return _ptr(t)
+
+
+# ------------------------------------------------------------------------- device calls
+def init(p: Params, rho, ux, uy, T, f, stream=None):
+    _check("lbm_init", _lib().lbm_init(ctypes.byref(p.c()), _field(p, rho, "rho"), _field(p, ux, "ux"),
+                                       _field(p, uy, "uy"), _field(p, T, "T"), _state(p, f, "f"),
+                                       _stream(stream)))
+    return f
+
+
+def step(p: Params, f_in, f_out, stream=None):
+    _check("lbm_step", _lib().lbm_step(ctypes.byref(p.c()), _state(p, f_in, "f_in"),
+                                       _state(p, f_out, "f_out"), _stream(stream)))
+    return f_out
+
+
+def run(p: Params, f_a, f_b, n_steps: int, stream=None):
+    """n_steps fused steps; returns the tensor holding the result."""
+    _check("lbm_run", _lib().lbm_run(ctypes.byref(p.c()), _state(p, f_a, "f_a"), _state(p, f_b, "f_b"),
+                                     int(n_steps), _stream(stream)))
+    return f_a if n_steps % 2 == 0 else f_b
+
+
+def propagate(p: Params, f_in, f_tmp, stream=None):
+    _check("lbm_propagate", _lib().lbm_propagate(ctypes.byref(p.c()), _state(p, f_in, "f_in"),
+                                                 _state(p, f_tmp, "f_tmp"), _stream(stream)))
+    return f_tmp
+
+
+def bc(p: Params, f_in, f_tmp, stream=None):
+    _check("lbm_bc", _lib().lbm_bc(ctypes.byref(p.c()), _state(p, f_in, "f_in"), _state(p, f_tmp, "f_tmp"),
+                                   _stream(stream)))
+    return f_tmp
+
+
+def collide(p: Params, f_tmp, f_out, stream=None):
+    _check("lbm_collide", _lib().lbm_collide(ctypes.byref(p.c()), _state(p, f_tmp, "f_tmp"),
+                                             _state(p, f_out, "f_out"), _stream(stream)))
+    return f_out
+
+
+def moments(p: Params, f, out=None, stream=None):
+    """(rho, ux, uy, T) of a state, each [lx, ly] float64 on the state's device."""
+    if out is None:
+        out = [torch.empty((p.lx, p.ly), dtype=torch.float64, device=f.device) for _ in range(4)]
+    rho, ux, uy, T = out
+    _check("lbm_moments", _lib().lbm_moments(ctypes.byref(p.c()), _state(p, f, "f"), _field(p, rho, "rho"),
+                                             _field(p, ux, "ux"), _field(p, uy, "uy"), _field(p, T, "T"),
+                                             _stream(stream)))
+    return rho, ux, uy, T
+
+
+def reduce_scratch_bytes(p: Params) -> int:
+    return _lib().lbm_reduce_scratch_bytes(ctypes.byref(p.c()))
+
+
+def kinetic_energy(p: Params, f, out=None, scratch=None, stream=None):
+    """Total kinetic energy as a 0-d float64 device tensor."""
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=f.device)
+    if scratch is None:
+        scratch = torch.empty(reduce_scratch_bytes(p) // 8, dtype=torch.float64, device=f.device)
+    _check("lbm_kinetic_energy", _lib().lbm_kinetic_energy(
+        ctypes.byref(p.c()), _state(p, f, "f"), _ptr(out), _ptr(scratch),
+        scratch.numel() * scratch.element_size(), _stream(stream)))
+    return out
+
+
+def simulate_host(p: Params, fields_in, n_steps: int, fields_out, f_a, f_b, fields_dev, stream=None):
+    """End-to-end run from host tensors (pinned for speed): fields in -> init -> n steps ->
+    moments -> fields out.  Synchronous."""
+    for t in list(fields_in) + list(fields_out):
+        if t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64 or t.numel() != p.lx * p.ly:
+            raise ValueError("host fields must be contiguous float64 CPU tensors of lx*ly elements")
+    if not (fields_dev.is_cuda and fields_dev.dtype == torch.float64 and fields_dev.numel() >= 4 * p.lx * p.ly):
+        raise ValueError("fields_dev must be a CUDA float64 tensor of 4*lx*ly elements")
+    fi = [_ptr(t) for t in fields_in]
+    fo = [_ptr(t) for t in fields_out]
+    _check("lbm_simulate_host", _lib().lbm_simulate_host(
+        ctypes.byref(p.c()), *fi, int(n_steps), *fo, _state(p, f_a, "f_a"), _state(p, f_b, "f_b"),
+        _ptr(fields_dev), _stream(stream)))
+    return fields_out

@@ -1,0 +1,96 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared entry point,
+its model constants satisfy the isotropy conditions and agree with the oracle's
+independently solved ones, and invalid arguments are rejected before any launch."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_1703_04594_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm_d2q37.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(lbm.LIB_PATH):
+        from paper_1703_04594_gb300 import build
+        build.build()
+    return lbm._lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lbm.exported_symbols()) == names
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(lbm, "_LIB", None)
+    monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        lbm.version()
+
+
+def gauss(n):
+    return 0 if n % 2 else math.prod(range(n - 1, 0, -2))
+
+
+def test_library_constants_satisfy_isotropy(lib):
+    c, w, vx, vy = lbm.model()
+    assert abs(sum(w) - 1.0) < 1e-15 and all(x > 0 for x in w)
+    for p in range(9):
+        for q in range(9 - p):
+            lhs = sum(wi * (c * a) ** p * (c * b) ** q for wi, a, b in zip(w, vx, vy))
+            assert abs(lhs - gauss(p) * gauss(q)) <= 2e-14 * max(1, gauss(p) * gauss(q)), (p, q)
+
+
+def test_library_constants_match_oracle(lib):
+    from oracle import d2q37 as M
+    c, w, vx, vy = lbm.model()
+    assert list(zip(vx, vy)) == M.VELOCITIES
+    assert abs(c - M.C_SCALE) <= 2e-16 * c
+    for a, b in zip(w, M.WEIGHTS.tolist()):
+        assert abs(a - b) <= 2e-16 * b
+
+
+def test_pitch_and_sizes(lib):
+    p = lbm.Params(64, 128)
+    assert lbm.pitch(p) == 128 and lbm.buffer_bytes(p) == 37 * 64 * 128 * 8
+    p = lbm.Params(37, 45)
+    assert lbm.pitch(p) == 64
+    p = lbm.Params(37, 45, precision=lbm.FP32_SHIFTED)
+    assert lbm.buffer_bytes(p) == 37 * 37 * 64 * 4
+
+
+@pytest.mark.parametrize("bad", [dict(lx=3), dict(ly=5), dict(tau=0.5), dict(tau=float("nan")),
+                                 dict(t_top=-1.0), dict(precision=7), dict(bc=3)])
+def test_invalid_params_rejected(lib, bad):
+    kw = dict(lx=8, ly=8)
+    kw.update(bad)
+    p = lbm.Params(**kw)
+    assert lib.lbm_pitch(ctypes.byref(p.c())) == -1
+    # rejected before any launch: the fake pointers are never touched
+    st = lib.lbm_step(ctypes.byref(p.c()), ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 30), None)
+    assert st == lbm.EINVAL
+
+
+def test_aliasing_and_alignment_rejected(lib):
+    p = lbm.Params(8, 8)
+    nbytes = lbm.buffer_bytes(p)
+    base = 1 << 32
+    assert lib.lbm_step(ctypes.byref(p.c()), ctypes.c_void_p(base), ctypes.c_void_p(base + nbytes // 2), None) == lbm.EINVAL
+    assert lib.lbm_step(ctypes.byref(p.c()), ctypes.c_void_p(base + 8), ctypes.c_void_p(base + 4 * nbytes), None) == lbm.EINVAL
+    assert lib.lbm_run(ctypes.byref(p.c()), ctypes.c_void_p(base), ctypes.c_void_p(base + 4 * nbytes), -1, None) == lbm.EINVAL
+    assert lib.lbm_strerror(lbm.EINVAL).startswith(b"invalid")
