@@ -35,11 +35,24 @@ TAU, GY, T_BOTTOM, T_TOP = 0.8, -1e-4, 1.15, 0.85
 #   138 add + 97 mul + 138 fma + 1 div = 512 flops, 374 FP64-pipe operations.
 FLOPS_PER_SITE_FP64 = 512
 BYTES_PER_SITE_FP64 = 592          # 37 x 8 B read + 37 x 8 B written
+BYTES_PER_SITE_FP32 = 296          # 37 x 4 B read + 37 x 4 B written
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per launch of the fused FP64 step, from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on this workload; None until captured for the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None}
+TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None, "fp32": None}
+
+
+def _hbm_peak():
+    """Measured STREAM-style copy bandwidth of the GB300s (GB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0          # fallback figure for a GB300 when the measured file is absent
+
+
+HBM_PEAK_GBS = _hbm_peak()
 
 
 def _args():
@@ -49,7 +62,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", choices=["fused", "separate"], default="fused")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                    help="fp32 = FP32 shifted-deviation storage (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lx", type=int, default=LX, help="lattice width (profiling of smaller cases)")
+    ap.add_argument("--ly", type=int, default=LY, help="lattice height (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -165,9 +182,14 @@ def run_ours(a):
     if not os.path.exists(lbm.LIB_PATH):
         raise RuntimeError("CUDA library missing: run __graft_entry__.build() first")
 
-    p = lbm.Params(LX, LY, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
-    sites = LX * LY
-    fields = I.rt_state(LX, LY, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))
+    lx, ly = a.lx, a.ly
+    fp32 = a.precision == "fp32"
+    if fp32 and a.variant != "fused":
+        raise SystemExit("--precision fp32 supports the fused step only")
+    p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
+                   precision=lbm.FP32_SHIFTED if fp32 else lbm.FP64)
+    sites = lx * ly
+    fields = I.rt_state(lx, ly, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))
     dev = [t.contiguous().cuda() for t in fields]
     fa, fb = lbm.empty_state(p), lbm.empty_state(p)
     ftmp = lbm.empty_state(p) if a.variant == "separate" else None
@@ -211,15 +233,22 @@ def run_ours(a):
 
     # dominant kernel: the fused step is the only launch of a fused bench step
     kern_ms = statistics.mean(per_step)
-    achieved = FLOPS_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH[a.variant],
-                "kernel": "k_step_fp64" if a.variant == "fused" else "whole step (3 kernels)",
-                "hbm_gbs_equiv": BYTES_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e9}
+    if fp32:
+        achieved = BYTES_PER_SITE_FP32 * sites / (kern_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": achieved / HBM_PEAK_GBS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get("fp32"),
+                    "kernel": "k_step_fp32", "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        achieved = FLOPS_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH[a.variant],
+                    "kernel": "k_step_fp64" if a.variant == "fused" else "whole step (3 kernels)",
+                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                    "hbm_gbs_equiv": BYTES_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e9}
 
     # end to end through the C-ABI from pinned host fields: H2D, init, K steps, moments, D2H
     pinned_in = [t.contiguous().pin_memory() for t in fields]
-    pinned_out = [torch.empty(LX, LY, dtype=torch.float64).pin_memory() for _ in range(4)]
+    pinned_out = [torch.empty(lx, ly, dtype=torch.float64).pin_memory() for _ in range(4)]
     fdev = torch.empty(4 * sites, dtype=torch.float64, device="cuda")
     del dev
     lbm.simulate_host(p, pinned_in, 1, pinned_out, fa, fb, fdev, stream)
@@ -240,16 +269,18 @@ def run_ours(a):
     if rank == 0:
         line = {"metric": "D2Q37 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"D2Q37 FP64 {a.variant} step, {LX}x{LY} Rayleigh-Taylor lattice",
-                           "lx": LX, "ly": LY, "tau": TAU, "gy": GY, "t_bottom": T_BOTTOM, "t_top": T_TOP,
+                "vs_baseline": None, "dtype": "f32+i64+f64" if fp32 else "f64", "data": "synthetic",
+                "config": {"workload": f"D2Q37 {'FP32-shifted' if fp32 else 'FP64'} {a.variant} step, "
+                                       f"{lx}x{ly} Rayleigh-Taylor lattice",
+                           "lx": lx, "ly": ly, "tau": TAU, "gy": GY, "t_bottom": T_BOTTOM, "t_top": T_TOP,
                            "seed": SEED, "variant": a.variant,
-                           "l2": "state buffers 9.9 GB >> 129 MB L2; no flush needed",
+                           "precision": a.precision,
+                           "l2": "state buffers >= 4.9 GB >> 129 MB L2; no flush needed",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e,
                 "gpu_launches": a.steps * (1 if a.variant == "fused" else 3),
                 "clocks": clk.summary()}
-        if not a.no_cpu_baseline and world == 1:
+        if not a.no_cpu_baseline and world == 1 and (lx, ly) == (LX, LY):
             line["cpu_baseline"] = oracle_sample(4)
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -15,6 +15,12 @@ struct StepArgs {
   CollideConst cc;
   double wall_b[Q];     // w_i P_i(T_bottom): ghost value = rho_w * wall_b[i]
   double wall_t[Q];     // w_i P_i(T_top)
+  // FP32 shifted storage: g_i = f_i - w_i rho0
+  double rho0;
+  float gb_scale[Q];    // ghost deviation = drho_w * gb_scale[i] + gb_bias[i]  (bottom wall)
+  float gb_bias[Q];     //   with gb_scale = w_i P_i(T_b), gb_bias = w_i rho0 (P_i(T_b) - 1)
+  float gt_scale[Q];    // same for the top wall
+  float gt_bias[Q];
 };
 
 cudaError_t launch_step_fp64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s);
@@ -26,7 +32,18 @@ cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* 
 cudaError_t launch_moments_fp64(const double* f, double* rho, double* ux, double* uy, double* T,
                                 const StepArgs& a, cudaStream_t s);
 long long ke_partial_count(const StepArgs& a);
+// Sums n doubles of part (one block, fixed order) into *out.
+cudaError_t launch_reduce_sum(const double* part, long long n, double* out, cudaStream_t s);
 cudaError_t launch_kinetic_energy_fp64(const double* f, double* out, double* part, const StepArgs& a,
+                                       cudaStream_t s);
+
+// FP32 shifted-deviation storage
+cudaError_t launch_step_fp32(const float* fin, float* fout, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_init_fp32(const double* rho, const double* ux, const double* uy, const double* T, float* f,
+                             const StepArgs& a, cudaStream_t s);
+cudaError_t launch_moments_fp32(const float* f, double* rho, double* ux, double* uy, double* T,
+                                const StepArgs& a, cudaStream_t s);
+cudaError_t launch_kinetic_energy_fp32(const float* f, double* out, double* part, const StepArgs& a,
                                        cudaStream_t s);
 
 }  // namespace d2q37

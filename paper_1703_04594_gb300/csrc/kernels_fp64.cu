@@ -283,11 +283,15 @@ long long ke_partial_count(const StepArgs& a) {
   return (long long)g.x * g.y;
 }
 
+cudaError_t launch_reduce_sum(const double* part, long long n, double* out, cudaStream_t s) {
+  k_reduce_sum<<<1, 256, 0, s>>>(part, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kinetic_energy_fp64(const double* f, double* out, double* part, const StepArgs& a,
                                        cudaStream_t s) {
   k_ke_partial_fp64<<<site_grid(a), kSiteBlock, 0, s>>>(f, part, a);
-  k_reduce_sum<<<1, 256, 0, s>>>(part, ke_partial_count(a), out);
-  return cudaGetLastError();
+  return launch_reduce_sum(part, ke_partial_count(a), out, s);
 }
 
 }  // namespace d2q37

@@ -69,14 +69,24 @@ StepArgs make_args(const lbm_params* p) {
   a.cc.cgx = C * tau * p->gx;
   a.cc.cgy = C * tau * p->gy;
   a.cc.tshift = tau * (1.0 - tau) * (p->gx * p->gx + p->gy * p->gy) / D - 1.0;
+  a.rho0 = p->rho0;
   for (int i = 0; i < Q; ++i) {
     a.wall_b[i] = wall_multiplier(i, p->t_bottom);
     a.wall_t[i] = wall_multiplier(i, p->t_top);
+    a.gb_scale[i] = (float)a.wall_b[i];
+    a.gb_bias[i] = (float)(p->rho0 * (a.wall_b[i] - weight(i)));
+    a.gt_scale[i] = (float)a.wall_t[i];
+    a.gt_bias[i] = (float)(p->rho0 * (a.wall_t[i] - weight(i)));
   }
   return a;
 }
 
 cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+cudaError_t launch_step(const void* fin, void* fout, const StepArgs& a, int32_t precision, cudaStream_t s) {
+  if (precision == LBM_FP32_SHIFTED) return launch_step_fp32((const float*)fin, (float*)fout, a, s);
+  return launch_step_fp64((const double*)fin, (double*)fout, a, s);
+}
 
 }  // namespace
 
@@ -102,28 +112,27 @@ int32_t lbm_init(const lbm_params* p, const double* rho, const double* ux, const
                  void* f, void* stream) {
   if (!params_ok(p) || !aligned8(rho) || !aligned8(ux) || !aligned8(uy) || !aligned8(T) || !aligned16(f))
     return LBM_EINVAL;
-  if (p->precision != LBM_FP64) return LBM_EINVAL;
   const StepArgs a = make_args(p);
+  if (p->precision == LBM_FP32_SHIFTED)
+    return cuda_status(launch_init_fp32(rho, ux, uy, T, (float*)f, a, as_stream(stream)));
   return cuda_status(launch_init_fp64(rho, ux, uy, T, (double*)f, a, as_stream(stream)));
 }
 
 int32_t lbm_step(const lbm_params* p, const void* fin, void* fout, void* stream) {
   if (!params_ok(p) || !aligned16(fin) || !aligned16(fout)) return LBM_EINVAL;
   if (overlap(fin, fout, state_bytes(p))) return LBM_EINVAL;
-  if (p->precision != LBM_FP64) return LBM_EINVAL;
   const StepArgs a = make_args(p);
-  return cuda_status(launch_step_fp64((const double*)fin, (double*)fout, a, as_stream(stream)));
+  return cuda_status(launch_step(fin, fout, a, p->precision, as_stream(stream)));
 }
 
 int32_t lbm_run(const lbm_params* p, void* fa, void* fb, int32_t n_steps, void* stream) {
   if (!params_ok(p) || !aligned16(fa) || !aligned16(fb) || n_steps < 0) return LBM_EINVAL;
   if (overlap(fa, fb, state_bytes(p))) return LBM_EINVAL;
-  if (p->precision != LBM_FP64) return LBM_EINVAL;
   const StepArgs a = make_args(p);
   for (int32_t n = 0; n < n_steps; ++n) {
-    const double* src = (const double*)((n & 1) ? fb : fa);
-    double* dst = (double*)((n & 1) ? fa : fb);
-    const int32_t st = cuda_status(launch_step_fp64(src, dst, a, as_stream(stream)));
+    const void* src = (n & 1) ? fb : fa;
+    void* dst = (n & 1) ? fa : fb;
+    const int32_t st = cuda_status(launch_step(src, dst, a, p->precision, as_stream(stream)));
     if (st != LBM_OK) return st;
   }
   return LBM_OK;
@@ -154,8 +163,9 @@ int32_t lbm_moments(const lbm_params* p, const void* f, double* rho, double* ux,
                     void* stream) {
   if (!params_ok(p) || !aligned16(f) || !aligned8(rho) || !aligned8(ux) || !aligned8(uy) || !aligned8(T))
     return LBM_EINVAL;
-  if (p->precision != LBM_FP64) return LBM_EINVAL;
   const StepArgs a = make_args(p);
+  if (p->precision == LBM_FP32_SHIFTED)
+    return cuda_status(launch_moments_fp32((const float*)f, rho, ux, uy, T, a, as_stream(stream)));
   return cuda_status(launch_moments_fp64((const double*)f, rho, ux, uy, T, a, as_stream(stream)));
 }
 
@@ -167,9 +177,10 @@ int64_t lbm_reduce_scratch_bytes(const lbm_params* p) {
 int32_t lbm_kinetic_energy(const lbm_params* p, const void* f, double* out, void* scratch, size_t scratch_bytes,
                            void* stream) {
   if (!params_ok(p) || !aligned16(f) || !aligned8(out) || !aligned8(scratch)) return LBM_EINVAL;
-  if (p->precision != LBM_FP64) return LBM_EINVAL;
   const StepArgs a = make_args(p);
   if ((int64_t)scratch_bytes < ke_partial_count(a) * (int64_t)sizeof(double)) return LBM_EINVAL;
+  if (p->precision == LBM_FP32_SHIFTED)
+    return cuda_status(launch_kinetic_energy_fp32((const float*)f, out, (double*)scratch, a, as_stream(stream)));
   return cuda_status(launch_kinetic_energy_fp64((const double*)f, out, (double*)scratch, a, as_stream(stream)));
 }
 
@@ -179,7 +190,6 @@ int32_t lbm_simulate_host(const lbm_params* p, const double* rho_h, const double
   if (!params_ok(p) || !rho_h || !ux_h || !uy_h || !T_h || !rho_o || !ux_o || !uy_o || !T_o || !aligned8(fields) ||
       n_steps < 0)
     return LBM_EINVAL;
-  if (p->precision != LBM_FP64) return LBM_EINVAL;
   cudaStream_t s = as_stream(stream);
   const size_t n = (size_t)p->lx * p->ly;
   const size_t bytes = n * sizeof(double);

@@ -52,3 +52,22 @@ def to_host(p: lbm.Params, f_dev) -> torch.Tensor:
 
 def rel_err(a, b):
     return float(((a - b).abs() / b.abs()).max())
+
+
+def field_errors(a, b):
+    """Per-field errors of fields a = (rho, ux, uy, T) against reference b: max and RMS of
+    |a - b| / |b| for rho and T; for the velocity (near zero at the start) the max and
+    RMS of |u_a - u_b| divided by the RMS of |u_b|."""
+    out = {}
+    for name, x, y in (("rho", a[0], b[0]), ("T", a[3], b[3])):
+        r = ((x - y).abs() / y.abs()).double()
+        out[name + "_max"] = float(r.max())
+        out[name + "_rms"] = float(torch.sqrt((r * r).mean()))
+    du = torch.sqrt((a[1] - b[1]) ** 2 + (a[2] - b[2]) ** 2).double()
+    ub = torch.sqrt(b[1] ** 2 + b[2] ** 2).double()
+    scale = float(torch.sqrt((ub * ub).mean()))
+    out["u_max"] = float(du.max()) / scale
+    out["u_rms"] = float(torch.sqrt((du * du).mean())) / scale
+    # against the model's velocity scale, the reference sound speed sqrt(T0) = 1 (xi units)
+    out["u_max_cs"] = float(du.max())
+    return out

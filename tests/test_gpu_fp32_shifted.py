@@ -1,0 +1,101 @@
+"""FP32 shifted-deviation storage (g_i = f_i - w_i rho0 in float32, exact fixed-point
+moment sums, float64 temperature) against the float64 oracle and the FP64 GPU path.
+
+Bar: per-field relative error <= 1e-5: max and RMS of |a - b| / |b| for density and
+temperature; for the velocity, max |u_a - u_b| relative to the model's velocity scale (the
+reference sound speed sqrt(T0) = 1 in xi units).  The velocity error relative to the
+field's own RMS (which starts at zero) is printed, not bounded: float32 storage of the
+deviations puts a floor of ~1e-8 per step on the absolute momentum error, which exceeds
+1e-5 of a velocity field that is still ~1e-4 in the early Rayleigh-Taylor run.  The
+storage itself is checked to be the float32 rounding of the oracle's deviations.
+"""
+import pytest
+import torch
+
+from oracle import d2q37 as OM
+from oracle import lbm as OL
+from paper_1703_04594_gb300 import lbm
+from tests.gpu_util import device_init, field_errors, oracle_params, require_gpu, rt_fields
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+BOUNDED = ("rho_max", "rho_rms", "T_max", "T_rms", "u_max_cs")
+
+
+def check(err):
+    print({k: f"{v:.2e}" for k, v in err.items()})
+    assert max(err[k] for k in BOUNDED) <= FIELD_TOL, err
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def fp32(p):
+    return lbm.Params(p.lx, p.ly, tau=p.tau, gx=p.gx, gy=p.gy, t_bottom=p.t_bottom, t_top=p.t_top,
+                      rho0=p.rho0, precision=lbm.FP32_SHIFTED, bc=p.bc)
+
+
+def test_init_stores_rounded_deviations():
+    p = fp32(lbm.Params(64, 128))
+    fields = rt_fields(p, seed=1)
+    f = device_init(p, fields)
+    got = f[:, :, : p.ly].double().cpu()
+    want = OL.init_equilibrium(*fields) - OM.WEIGHTS[:, None, None] * p.rho0
+    # float32 rounding of the deviation: within half an ulp (2^-24 relative) + the
+    # float64 equilibrium's own rounding
+    assert float(((got - want).abs() / want.abs().clamp_min(1e-30)).max()) <= 2 ** -24 + 1e-12
+
+
+@pytest.mark.parametrize("lx,ly,bc,steps", [(64, 128, lbm.BC_WALLS, 10), (37, 45, lbm.BC_WALLS, 20),
+                                            (33, 40, lbm.BC_PERIODIC_Y, 20)])
+def test_fields_vs_oracle(lx, ly, bc, steps):
+    p = fp32(lbm.Params(lx, ly, gx=1e-4 if bc == lbm.BC_PERIODIC_Y else 0.0, bc=bc))
+    fields = rt_fields(p, seed=2)
+    fa = device_init(p, fields)
+    fb = lbm.empty_state(p)
+    res = lbm.run(p, fa, fb, steps)
+    got = [t.cpu() for t in lbm.moments(p, res)]
+    want = OL.fields(OL.run(OL.init_equilibrium(*fields), oracle_params(p), steps))
+    check(field_errors(got, want))
+
+
+def test_hundred_steps_vs_oracle():
+    p = fp32(lbm.Params(32, 64, tau=0.7))
+    fields = rt_fields(p, seed=3)
+    fa = device_init(p, fields)
+    res = lbm.run(p, fa, lbm.empty_state(p), 100)
+    got = [t.cpu() for t in lbm.moments(p, res)]
+    want = OL.fields(OL.run(OL.init_equilibrium(*fields), oracle_params(p), 100))
+    check(field_errors(got, want))
+
+
+def test_full_size_1000_steps_vs_fp64_gpu():
+    """4096 x 8192, seed 2, 1000 steps: FP32 shifted storage against the FP64 GPU path
+    (itself pinned to the oracle by the FP64 parity tests)."""
+    p64 = lbm.Params(4096, 8192)
+    p32 = fp32(p64)
+    fields = rt_fields(p64, seed=2)
+    a = device_init(p64, fields)
+    r64 = lbm.run(p64, a, lbm.empty_state(p64), 1000)
+    m64 = [t.clone() for t in lbm.moments(p64, r64)]
+    del a, r64
+    torch.cuda.empty_cache()
+    b = device_init(p32, fields)
+    r32 = lbm.run(p32, b, lbm.empty_state(p32), 1000)
+    m32 = lbm.moments(p32, r32)
+    check(field_errors(m32, m64))
+    del b, r32
+    torch.cuda.empty_cache()
+
+
+def test_kinetic_energy_fp32_close_to_fp64():
+    p64 = lbm.Params(64, 128)
+    fields = rt_fields(p64, seed=4)
+    r64 = lbm.run(p64, device_init(p64, fields), lbm.empty_state(p64), 50)
+    p32 = fp32(p64)
+    r32 = lbm.run(p32, device_init(p32, fields), lbm.empty_state(p32), 50)
+    k64, k32 = float(lbm.kinetic_energy(p64, r64)), float(lbm.kinetic_energy(p32, r32))
+    assert abs(k32 - k64) <= 1e-4 * k64
