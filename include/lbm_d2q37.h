@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, LBM_ENOMEM = 4 };
+enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, LBM_ENOMEM = 4, LBM_ESIZE = 5 };
 enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
 enum lbm_bc { LBM_BC_WALLS = 0, LBM_BC_PERIODIC_Y = 1 /* test mode: y wraps like x */ };
 
@@ -116,6 +116,22 @@ int64_t lbm_reduce_scratch_bytes(const lbm_params* p);
  * summed in a fixed order by one block. */
 int32_t lbm_kinetic_energy(const lbm_params* p, const void* f_dev, double* out_dev,
                            void* scratch_dev, size_t scratch_bytes, void* stream);
+
+/* Kinetic energy exactly as lbm_kinetic_energy, for callers that cannot allocate device
+ * memory while they run (for example an application whose device memory is all reserved
+ * up front by its own pool, or a time-critical stepping loop that must not call cudaMalloc,
+ * which can synchronise the device).  The paper has no counterpart: this is a library
+ * convenience.  Nothing is allocated: the per-tile partial sums go to a fixed array of
+ * LBM_NOALLOC_MAX_TILES doubles (2 MiB) built into the library, which every GPU that loads
+ * the library holds until the process exits.  A lattice needs ceil(ly/32) * ceil(lx/4)
+ * tiles (4096 x 8192 needs exactly the maximum); larger lattices return LBM_ESIZE.
+ * The first call on each device looks up the array's device address (and may load the
+ * library's device code); make that first call before any stream capture.  All calls share
+ * the array and leave their partial sums in it; each call only reads what it has just
+ * written, so no clearing is needed, but calls whose kernels can overlap on the GPU (on
+ * different streams without ordering) race on it. */
+#define LBM_NOALLOC_MAX_TILES 262144
+int32_t lbm_kinetic_energy_noalloc(const lbm_params* p, const void* f_dev, double* out_dev, void* stream);
 
 /* End-to-end run from host memory (synchronous): copies the four initial fields from
  * host (pinned for best speed) to fields_dev (4 * lx * ly doubles, device), builds the

@@ -220,6 +220,7 @@ const char* lbm_strerror(int32_t status) {
     case LBM_ECUDA: return "CUDA launch or copy failed (see lbm_last_cuda_error)";
     case LBM_ETIMEOUT: return "device-side wait exceeded its iteration limit";
     case LBM_ENOMEM: return "out of memory";
+    case LBM_ESIZE: return "lattice needs more than LBM_NOALLOC_MAX_TILES tiles of fixed scratch";
     default: return "unknown status";
   }
 }

@@ -20,7 +20,8 @@ FP64, FP32_SHIFTED = 0, 1
 BC_WALLS, BC_PERIODIC_Y = 0, 1
 Q = 37
 
-OK, EINVAL, ECUDA, ETIMEOUT, ENOMEM = 0, 1, 2, 3, 4
+OK, EINVAL, ECUDA, ETIMEOUT, ENOMEM, ESIZE = 0, 1, 2, 3, 4, 5
+NOALLOC_MAX_TILES = 262144
 
 
 class CParams(ctypes.Structure):
@@ -79,6 +80,7 @@ _SIGS = {
     "lbm_moments": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "lbm_reduce_scratch_bytes": (ctypes.c_int64, [_PP]),
     "lbm_kinetic_energy": (ctypes.c_int32, [_PP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "lbm_kinetic_energy_noalloc": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_simulate_host": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
                                            _VP, _VP, _VP, _VP]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -235,6 +237,19 @@ def kinetic_energy(p: Params, f, out=None, scratch=None, stream=None):
     _check("lbm_kinetic_energy", _lib().lbm_kinetic_energy(
         ctypes.byref(p.c()), _state(p, f, "f"), _ptr(out), _ptr(scratch),
         scratch.numel() * scratch.element_size(), _stream(stream)))
+    return out
+
+
+def kinetic_energy_noalloc(p: Params, f, out=None, stream=None):
+    """Total kinetic energy without scratch from the caller: for callers that cannot
+    allocate device memory while running (memory fully reserved up front, or loops that
+    must not call cudaMalloc).  The partial sums go to a fixed array inside the library
+    (LBM_NOALLOC_MAX_TILES doubles per GPU); larger lattices raise LbmError (LBM_ESIZE).
+    Calls that overlap on the GPU race on that array.  ``out`` is the only device buffer."""
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=f.device)
+    _check("lbm_kinetic_energy_noalloc", _lib().lbm_kinetic_energy_noalloc(
+        ctypes.byref(p.c()), _state(p, f, "f"), _ptr(out), _stream(stream)))
     return out
 
 
