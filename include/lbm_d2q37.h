@@ -31,7 +31,7 @@
  *   - Return value: LBM_OK, or an lbm_status error code.  Invalid arguments are
  *     rejected with LBM_EINVAL before anything is launched.  LBM_ECUDA reports a launch
  *     or copy failure; lbm_last_cuda_error() returns the CUDA error code.
- *   - State buffers must be 256-byte aligned (cudaMalloc and torch guarantee it); a
+ *   - State buffers must be 16-byte aligned (cudaMalloc and torch give 256); a
  *     step's input and output must not overlap (the pull scheme needs two copies).
  */
 #ifndef LBM_D2Q37_H
