@@ -65,6 +65,9 @@ def _args():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32 = FP32 shifted-deviation storage (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+                    help="batch = 256 independent lattices of uneven sizes (persistent launch)")
+    ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--lx", type=int, default=LX, help="lattice width (profiling of smaller cases)")
     ap.add_argument("--ly", type=int, default=LY, help="lattice height (profiling of smaller cases)")
     return ap.parse_args()
@@ -287,10 +290,85 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_batch(a):
+    """Batched form: independent RT lattices (Lx in 128..1024 step 64 drawn by seed 4,
+    Ly = 2 Lx, tau ~ U[0.6, 1.0], own interface seeds) stepped by one persistent launch
+    (autotuned), against looping the single-lattice kernel over the lattices."""
+    import torch
+
+    from paper_1703_04594_gb300 import inputs as I
+    from paper_1703_04594_gb300 import lbm
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    fp32 = a.precision == "fp32"
+    prec = lbm.FP32_SHIFTED if fp32 else lbm.FP64
+    spec = I.batch_workload(seed=4 + rank, n=a.batch_n)
+    params, fa, fb = [], [], []
+    for lx, ly, tau, s in spec:
+        p = lbm.Params(lx, ly, tau=tau, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP, precision=prec)
+        params.append(p)
+        fa.append(lbm.empty_state(p))
+        fb.append(lbm.empty_state(p))
+    b = lbm.Batch(params, fa, fb)
+    cfg = b.autotune(trial_steps=2)                       # on the not-yet-initialised buffers
+    for (lx, ly, tau, s), p, t in zip(spec, params, fa):
+        dev = [x.contiguous().cuda() for x in I.rt_state(lx, ly, s, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))]
+        lbm.init(p, *dev, t)
+    b.close()
+    b = lbm.Batch(params, fa, fb)
+    b.configure(cfg["mode"], cfg["warps_per_block"], cfg["blocks_per_sm"], cfg["strips_per_chunk"])
+    sites = b.sites()
+    stream = torch.cuda.current_stream()
+
+    def timed(mode_cfg, steps):
+        b.configure(*mode_cfg)
+        b.run(a.warmup, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(steps, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if b.status() != lbm.OK:
+            raise RuntimeError("batched run reported a barrier timeout")
+        return e0.elapsed_time(e1)
+
+    with ClockSampler(local) as clk:
+        ms = timed((cfg["mode"], cfg["warps_per_block"], cfg["blocks_per_sm"], cfg["strips_per_chunk"]), a.steps)
+    ms_loop = timed((lbm.BATCH_LOOP, 4, 0, 1), a.steps)
+    value = sites * a.steps / (ms * 1e-3) / 1e6
+    bytes_site = BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64
+    if fp32:
+        achieved = bytes_site * sites * a.steps / (ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": achieved / HBM_PEAK_GBS, "traffic": None, "kernel": "k_batch_persistent<float>"}
+    else:
+        achieved = FLOPS_PER_SITE_FP64 * sites * a.steps / (ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_batch_persistent<double>"}
+    if rank == 0:
+        line = {"metric": "D2Q37 MLUPS (batched)", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64" if fp32 else "f64",
+                "data": "synthetic",
+                "config": {"workload": f"{len(spec)} RT lattices, Lx in 128..1024, Ly = 2 Lx, tau in [0.6, 1.0]",
+                           "sites": sites, "precision": a.precision, "autotuned": cfg,
+                           "l2": "states total >> 129 MB L2"},
+                "loop_baseline": {"value": sites * a.steps / (ms_loop * 1e-3) / 1e6, "unit": "MLUPS",
+                                  "what": "single-lattice kernel launched per lattice per step"},
+                "roofline": roofline, "gpu_launches": a.steps if cfg["mode"] == lbm.BATCH_PER_STEP else 1,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
     else:
         run_ours(a)
 

@@ -51,7 +51,7 @@ enum lbm_bc { LBM_BC_WALLS = 0, LBM_BC_PERIODIC_Y = 1 /* test mode: y wraps like
 /* Problem parameters, as the paper states the problem (Sec. 3): lattice size, BGK
  * relaxation time tau (> 0.5), gravity (gx, gy) per time step in xi units, wall
  * temperatures.  rho0 is the reference density of the FP32_SHIFTED storage.
- * Constraints: lx >= 4, ly >= 6, lx * ly * 37 < 2^40. */
+ * Constraints: lx >= 4, ly >= 6, lx * lbm_pitch < 2^32, lx <= 262140. */
 typedef struct lbm_params {
   int32_t lx, ly;
   int32_t precision; /* enum lbm_precision */
@@ -143,6 +143,73 @@ int32_t lbm_simulate_host(const lbm_params* p, const double* rho_host, const dou
                           double* rho_out_host, double* ux_out_host, double* uy_out_host,
                           double* T_out_host, void* f_a_dev, void* f_b_dev, double* fields_dev,
                           void* stream);
+
+/* ---- Adjoint (reverse mode) of the FP64 step, for gradients of observables ----
+ * The paper steps forward only; these are the transposed Jacobians of the same operations
+ * (propagate and bc are linear, collide is differentiated site by site through the
+ * moments of eq. "macro", the gravity shift and the Hermite equilibrium).  FP64 only. */
+/* Bytes of workspace lbm_adjoint_step needs: one state buffer plus per-tile partials. */
+int64_t lbm_adjoint_work_bytes(const lbm_params* p);
+/* lam_n = (d step / d f_n)^T lam_next, and *dtau_accum += lam_next . d step(f_n) / d tau
+ * (deterministic per-tile partials summed in a fixed order).  f_n is the state the forward
+ * step started from (recomputed or checkpointed by the caller); lam_* are state-shaped
+ * buffers; work_dev holds lbm_adjoint_work_bytes bytes.  lam_n must not alias lam_next. */
+int32_t lbm_adjoint_step(const lbm_params* p, const void* f_n_dev, const void* lam_next_dev, void* lam_n_dev,
+                         double* dtau_accum_dev, void* work_dev, size_t work_bytes, void* stream);
+/* lam = d E / d f for the total kinetic energy E = sum 1/2 rho |u|^2 of state f. */
+int32_t lbm_kinetic_energy_grad(const lbm_params* p, const void* f_dev, void* lam_dev, void* stream);
+/* Gradients of the initial fields of lbm_init against lam0 = dL/df^0:
+ * g_X = sum_i lam0_i d f_i^eq(rho, u, T) / dX for X in (rho, ux, uy, T); [lx][ly] doubles. */
+int32_t lbm_init_adjoint(const lbm_params* p, const double* rho_dev, const double* ux_dev, const double* uy_dev,
+                         const double* T_dev, const void* lam0_dev, double* g_rho_dev, double* g_ux_dev,
+                         double* g_uy_dev, double* g_T_dev, void* stream);
+
+/* ---- Batched stepping of many independent lattices (uneven sizes, own tau, walls...) ----
+ * The paper steps one lattice per process; this runs many independent problems in one
+ * launch so that small lattices fill the GPU (its start-up mini-benchmark tuning, Sec. 6,
+ * becomes the autotuner below).  All lattices of a batch share precision and bc mode; each
+ * has its own lbm_params and its own two state buffers.  Results are bit-identical to
+ * lbm_run on each lattice. */
+typedef struct lbm_batch lbm_batch;
+enum lbm_batch_mode {
+  LBM_BATCH_PER_STEP = 1,   /* one launch per step over every strip of every lattice */
+  LBM_BATCH_PERSISTENT = 2, /* one cooperative launch for all steps, grid barrier between steps */
+  LBM_BATCH_LOOP = 3        /* the single-lattice kernel launched per lattice (baseline) */
+};
+/* Validates n lattices and binds their buffers (f_a_dev[j], f_b_dev[j]: device states of
+ * lbm_buffer_bytes(&params[j]) bytes, current state in f_a).  Allocates the batch's own
+ * device descriptor table and barrier word (the only allocating entry point; freed by
+ * lbm_batch_destroy).  Synchronous.  Default configuration: persistent, 4 warps per block,
+ * as many blocks per SM as fit, 1 strip per chunk. */
+int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a_dev, void* const* f_b_dev, int32_t n,
+                       lbm_batch** out);
+/* Sets mode, warps per block (1, 2, 4, 8), blocks per SM (persistent only; 0 = all that fit)
+ * and the tile shape: strips_per_chunk (1..64) consecutive 32-row strips of one column
+ * handled by one warp per work item.  Synchronous when the tile shape changes. */
+int32_t lbm_batch_configure(lbm_batch* b, int32_t mode, int32_t warps_per_block, int32_t blocks_per_sm,
+                            int32_t strips_per_chunk);
+/* Reads the configuration (blocks_per_sm: the value the persistent launch uses, else 0). */
+int32_t lbm_batch_config(const lbm_batch* b, int32_t* mode, int32_t* warps_per_block, int32_t* blocks_per_sm,
+                         int32_t* strips_per_chunk);
+/* Times every candidate configuration for trial_steps steps (after one warm-up step each)
+ * and keeps the fastest.  It ADVANCES the batch by (trial_steps + 1) steps per candidate:
+ * call it before initialising the states, or on states whose evolution does not matter.
+ * Synchronous. */
+int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream);
+/* n_steps steps of every lattice in the current configuration; stream-ordered. */
+int32_t lbm_batch_run(lbm_batch* b, int32_t n_steps, void* stream);
+/* Which buffer holds the current states: 0 = f_a, 1 = f_b (flips with every odd run). */
+int32_t lbm_batch_parity(const lbm_batch* b);
+/* Total fluid sites of the batch. */
+int64_t lbm_batch_sites(const lbm_batch* b);
+/* Synchronous: LBM_OK, or LBM_ETIMEOUT if a persistent run's grid-barrier wait expired
+ * (the run then stopped early and the states are undefined); clears the error word. */
+int32_t lbm_batch_status(lbm_batch* b);
+/* Grid-barrier wait limit in ns (default 2 s, at most 60 s).  phantom_arrivals makes every
+ * barrier wait for that many extra blocks that never arrive: a test hook that forces the
+ * wait to expire (0 in normal use). */
+int32_t lbm_batch_set_wait(lbm_batch* b, int64_t timeout_ns, int32_t phantom_arrivals);
+void lbm_batch_destroy(lbm_batch* b);
 
 /* Human-readable text of an lbm_status code. */
 const char* lbm_strerror(int32_t status);

@@ -1,0 +1,313 @@
+// Hand-written adjoint (vector-Jacobian product) of the FP64 fused step, and of the
+// equilibrium initialisation and the kinetic-energy observable.
+//
+// The step is S = C o B o P: pull propagate P and wall bc B are linear in f (a ghost value
+// is rho_w(x_s) * w_i P_i(T_wall), rho_w a sum of the source column's wall-row
+// populations); collide C acts site by site (Sec. 3, eqs. "lbequation", "macro").  For
+// lambda' = dL/df^{n+1}:
+//   1. (k_adj_collide) at every site, recompute f~ = B P f^n and its moments, then
+//        mu_i = lambda'_i,
+//        out_i = (1 - w) mu_i + w (nu_rho + nu_J . xi_i + nu_E |xi_i|^2),   w = 1/tau,
+//      where nu = (d f^eq / d(rho, J, E))^T mu through u = J/rho,
+//      T = (E/rho - |u|^2)/D, the gravity shift u_s = u + tau g, T_s = T + tau(1-tau)|g|^2/D
+//      and the fourth-order Hermite polynomial; the site's contribution to dL/dtau is
+//        sum_i mu_i d f_i'/d tau = -(1/tau^2) sum_i mu_i (f^eq_i - f~_i)
+//                                   + w [G_u . g + G_t (1 - 2 tau) |g|^2 / D];
+//   2. (k_adj_propagate) lambda_i(x, y) = out_i(x + v_i) for destinations inside the fluid
+//      (the transpose of the pull), plus, on the wall rows, the transpose of the ghost
+//      values: every population of (x_s, 0) receives sum over the ghost-fed entries
+//      (x_s + vx_i, y') of out_i(x_s + vx_i, y') * w_i P_i(T_bottom), and likewise at the top.
+// dL/dtau partials are summed per block and then in a fixed order (deterministic).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm_d2q37.h"
+#include "kernels.h"
+#include "step_fp64.cuh"
+
+namespace d2q37 {
+
+namespace {
+
+// Vector-Jacobian product of the equilibrium f^eq_i = w_i rho P_i(s_i, U, t),
+// s_i = xi_i . u_s, U = |u_s|^2, t = T_s - 1, against mu: returns
+//   Grho = sum mu_i w_i P_i,            (d/d rho at fixed u_s, t)
+//   Gu   = rho sum mu_i w_i (dP/ds xi_i + 2 dP/dU u_s),
+//   Gt   = rho sum mu_i w_i dP/dt.
+struct EqVjp {
+  double Grho, Gux, Guy, Gt;
+};
+
+__device__ __forceinline__ EqVjp eq_vjp(double rho, double usx, double usy, double t, const double (&mu)[Q]) {
+  const double U = fma(usx, usx, usy * usy);
+  double Gr = 0.0, Gx = 0.0, Gy = 0.0, Gt = 0.0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double q = C2 * (double)v2(i);
+    const double xix = C * (double)vx(i), xiy = C * (double)vy(i);
+    const double s = fma(xix, usx, xiy * usy);
+    const double c2 = 0.5 - 0.25 * U + 0.25 * t * (q - D - 4.0);
+    const double c1 = 1.0 - 0.5 * U + 0.5 * t * (q - D - 2.0);
+    const double c0 = 1.0 - 0.5 * U + 0.5 * t * (q - D) + 0.125 * U * U + 0.25 * t * U * (D + 2.0 - q) +
+                      0.125 * t * t * (q * q - 2.0 * (D + 2.0) * q + D * (D + 2.0));
+    const double P = fma(s, fma(s, fma(s, fma(s, 1.0 / 24.0, 1.0 / 6.0), c2), c1), c0);
+    const double Ps = fma(s, fma(s, fma(s, 1.0 / 6.0, 0.5), 2.0 * c2), c1);
+    const double PU = (-0.5 + 0.25 * U + 0.25 * t * (D + 2.0 - q)) - 0.5 * s - 0.25 * s * s;
+    const double Pt = (0.5 * (q - D) + 0.25 * U * (D + 2.0 - q) +
+                       0.25 * t * (q * q - 2.0 * (D + 2.0) * q + D * (D + 2.0))) +
+                      0.5 * (q - D - 2.0) * s + 0.25 * (q - D - 4.0) * s * s;
+    const double m = mu[i] * weight(i);
+    Gr = fma(m, P, Gr);
+    Gx = fma(m, fma(Ps, xix, 2.0 * PU * usx), Gx);
+    Gy = fma(m, fma(Ps, xiy, 2.0 * PU * usy), Gy);
+    Gt = fma(m, Pt, Gt);
+  }
+  return {Gr, rho * Gx, rho * Gy, rho * Gt};
+}
+
+__device__ __forceinline__ double block_sum_128(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __shared__ double ws[4];
+  const int w = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if ((threadIdx.x & 31) == 0) ws[w] = v;
+  __syncthreads();
+  return (ws[0] + ws[1]) + (ws[2] + ws[3]);
+}
+
+}  // namespace
+
+// Step 1: per-site adjoint of the collision (block 32 x 4 as the forward kernels).
+template <bool PERIODIC>
+__global__ void __launch_bounds__(128) k_adj_collide(const double* __restrict__ fin,
+                                                     const double* __restrict__ lam_next, double* __restrict__ out,
+                                                     double* __restrict__ dtau_part, StepArgs a, double tau, double gx,
+                                                     double gy) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y0 = blockIdx.x * 32;
+  const int y = y0 + threadIdx.x;
+  double contrib = 0.0;
+  if (x < a.lx) {  // uniform per warp
+    const bool active = y < a.ly;
+    const int yc = active ? y : a.ly - 1;
+    double f[Q];
+    gather_strip_fp64<PERIODIC>(fin, a, a, x, y0, yc, f, LdReadOnly());
+    if (active) {
+      double rho, jx, jy, e;
+      moments_int(f, rho, jx, jy, e);
+      const double inv = 1.0 / rho;
+      const double Jx = C * jx, Jy = C * jy, E = C2 * e;  // xi-unit moments
+      const double ux = Jx * inv, uy = Jy * inv;
+      const double uu = fma(ux, ux, uy * uy);
+      const double T = (E * inv - uu) / D;
+      const double gg = fma(gx, gx, gy * gy);
+      const double usx = fma(tau, gx, ux), usy = fma(tau, gy, uy);
+      const double t = T + tau * (1.0 - tau) * gg / D - 1.0;
+      const long long o = (long long)x * a.pitch + y;
+      double mu[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) mu[i] = __ldg(lam_next + o + i * a.pop);
+      const EqVjp G = eq_vjp(rho, usx, usy, t, mu);
+      const double nuE = G.Gt * inv / D;
+      const double nuJx = G.Gux * inv - 2.0 * ux * G.Gt * inv / D;
+      const double nuJy = G.Guy * inv - 2.0 * uy * G.Gt * inv / D;
+      const double nuR = G.Grho - (G.Gux * ux + G.Guy * uy) * inv + G.Gt * (-E * inv + 2.0 * uu) * inv / D;
+      const double om = 1.0 / tau, om1 = 1.0 - om;
+      double mu_ft = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double xix = C * (double)vx(i), xiy = C * (double)vy(i), q = C2 * (double)v2(i);
+        const double v = fma(om1, mu[i], om * (nuR + nuJx * xix + nuJy * xiy + nuE * q));
+        __stcs(out + o + i * a.pop, v);
+        mu_ft = fma(mu[i], f[i], mu_ft);
+      }
+      // sum_i mu_i f^eq_i = rho * Grho
+      contrib = -(rho * G.Grho - mu_ft) * om * om + om * (G.Gux * gx + G.Guy * gy + G.Gt * (1.0 - 2.0 * tau) * gg / D);
+    }
+  }
+  const double s = block_sum_128(contrib);
+  if (threadIdx.x == 0 && threadIdx.y == 0) dtau_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// Step 2: transpose of pull propagate + wall bc.  One thread per site.
+template <bool PERIODIC>
+__global__ void __launch_bounds__(128) k_adj_propagate(const double* __restrict__ out, double* __restrict__ lam,
+                                                       StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  double wall = 0.0;
+  if (!PERIODIC && y == 0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (vy(i) <= 0) continue;
+      const double* src = out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch;
+      double s = 0.0;
+      for (int yp = 0; yp < vy(i) && yp < a.ly; ++yp) s += __ldg(src + yp);
+      wall = fma(s, a.wall_b[i], wall);
+    }
+  }
+  if (!PERIODIC && y == a.ly - 1) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (vy(i) >= 0) continue;
+      const double* src = out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch;
+      double s = 0.0;
+      for (int yp = a.ly + vy(i); yp < a.ly; ++yp) s += __ldg(src + yp);
+      wall = fma(s, a.wall_t[i], wall);
+    }
+  }
+  double* dst = lam + (long long)x * a.pitch + y;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int yd = y + vy(i);
+    double v = 0.0;
+    if (PERIODIC) {
+      yd = wrap_index(yd, a.ly);
+      v = __ldg(out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch + yd);
+    } else if (yd >= 0 && yd < a.ly) {
+      v = __ldg(out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch + yd);
+    }
+    __stcs(dst + i * a.pop, v + wall);
+  }
+}
+
+// Adds sum(part[0..n)) to *acc in a fixed order (one block).
+__global__ void __launch_bounds__(256) k_reduce_add(const double* __restrict__ part, long long n, double* acc) {
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    *acc += t;
+  }
+}
+
+// dE/df_i for E = sum 1/2 |J|^2 / rho:  -|u|^2/2 + u . xi_i.
+__global__ void __launch_bounds__(128) k_ke_grad(const double* __restrict__ f, double* __restrict__ lam, StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  const long long o = (long long)x * a.pitch + y;
+  double g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) g[i] = __ldg(f + o + i * a.pop);
+  double rho, jx, jy, e;
+  moments_int(g, rho, jx, jy, e);
+  const double ux = C * jx / rho, uy = C * jy / rho;
+  const double h = -0.5 * fma(ux, ux, uy * uy);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) lam[o + i * a.pop] = h + C * (ux * (double)vx(i) + uy * (double)vy(i));
+}
+
+// Gradient of f^0 = f^eq(rho, u, T) with respect to the four fields, against lambda^0.
+__global__ void __launch_bounds__(128) k_init_adjoint(const double* __restrict__ rho, const double* __restrict__ ux,
+                                                      const double* __restrict__ uy, const double* __restrict__ T,
+                                                      const double* __restrict__ lam, double* __restrict__ g_rho,
+                                                      double* __restrict__ g_ux, double* __restrict__ g_uy,
+                                                      double* __restrict__ g_T, StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  const long long fi = (long long)x * a.ly + y;
+  const long long o = (long long)x * a.pitch + y;
+  double mu[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) mu[i] = __ldg(lam + o + i * a.pop);
+  const EqVjp G = eq_vjp(rho[fi], ux[fi], uy[fi], T[fi] - 1.0, mu);
+  g_rho[fi] = G.Grho;
+  g_ux[fi] = G.Gux;
+  g_uy[fi] = G.Guy;
+  g_T[fi] = G.Gt;
+}
+
+static inline dim3 site_grid(const StepArgs& a) { return dim3((a.ly + 31) / 32, (a.lx + 3) / 4); }
+
+long long adjoint_partial_count(const StepArgs& a) {
+  const dim3 g = site_grid(a);
+  return (long long)g.x * g.y;
+}
+
+cudaError_t launch_adjoint_step(const double* fin, const double* lam_next, double* lam, double* out, double* part,
+                                double* dtau, const StepArgs& a, double tau, double gx, double gy, cudaStream_t s) {
+  const dim3 blk(32, 4);
+  if (a.periodic) {
+    k_adj_collide<true><<<site_grid(a), blk, 0, s>>>(fin, lam_next, out, part, a, tau, gx, gy);
+    k_adj_propagate<true><<<site_grid(a), blk, 0, s>>>(out, lam, a);
+  } else {
+    k_adj_collide<false><<<site_grid(a), blk, 0, s>>>(fin, lam_next, out, part, a, tau, gx, gy);
+    k_adj_propagate<false><<<site_grid(a), blk, 0, s>>>(out, lam, a);
+  }
+  k_reduce_add<<<1, 256, 0, s>>>(part, adjoint_partial_count(a), dtau);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ke_grad(const double* f, double* lam, const StepArgs& a, cudaStream_t s) {
+  k_ke_grad<<<site_grid(a), dim3(32, 4), 0, s>>>(f, lam, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_adjoint(const double* rho, const double* ux, const double* uy, const double* T,
+                                const double* lam, double* g_rho, double* g_ux, double* g_uy, double* g_T,
+                                const StepArgs& a, cudaStream_t s) {
+  k_init_adjoint<<<site_grid(a), dim3(32, 4), 0, s>>>(rho, ux, uy, T, lam, g_rho, g_ux, g_uy, g_T, a);
+  return cudaGetLastError();
+}
+
+}  // namespace d2q37
+
+using namespace d2q37;
+
+namespace {
+
+int32_t status_of(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+bool a16(const void* p) { return p && ((uintptr_t)p % 16) == 0; }
+bool a8(const void* p) { return p && ((uintptr_t)p % 8) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int64_t lbm_adjoint_work_bytes(const lbm_params* p) {
+  if (!params_valid(p) || p->precision != LBM_FP64) return -1;
+  const StepArgs a = make_step_args(p);
+  return lbm_buffer_bytes(p) + adjoint_partial_count(a) * (int64_t)sizeof(double);
+}
+
+int32_t lbm_adjoint_step(const lbm_params* p, const void* f_n, const void* lam_next, void* lam_n, double* dtau_accum,
+                         void* work, size_t work_bytes, void* stream) {
+  if (!params_valid(p) || p->precision != LBM_FP64 || !a16(f_n) || !a16(lam_next) || !a16(lam_n) ||
+      !a8(dtau_accum) || !a16(work))
+    return LBM_EINVAL;
+  const int64_t need = lbm_adjoint_work_bytes(p);
+  if ((int64_t)work_bytes < need || lam_next == lam_n || f_n == lam_n) return LBM_EINVAL;
+  const StepArgs a = make_step_args(p);
+  double* out = (double*)work;
+  double* part = (double*)((char*)work + lbm_buffer_bytes(p));
+  return status_of(launch_adjoint_step((const double*)f_n, (const double*)lam_next, (double*)lam_n, out, part,
+                                       dtau_accum, a, p->tau, p->gx, p->gy, (cudaStream_t)stream));
+}
+
+int32_t lbm_kinetic_energy_grad(const lbm_params* p, const void* f, void* lam, void* stream) {
+  if (!params_valid(p) || p->precision != LBM_FP64 || !a16(f) || !a16(lam) || f == lam) return LBM_EINVAL;
+  const StepArgs a = make_step_args(p);
+  return status_of(launch_ke_grad((const double*)f, (double*)lam, a, (cudaStream_t)stream));
+}
+
+int32_t lbm_init_adjoint(const lbm_params* p, const double* rho, const double* ux, const double* uy, const double* T,
+                         const void* lam0, double* g_rho, double* g_ux, double* g_uy, double* g_T, void* stream) {
+  if (!params_valid(p) || p->precision != LBM_FP64 || !a8(rho) || !a8(ux) || !a8(uy) || !a8(T) || !a16(lam0) ||
+      !a8(g_rho) || !a8(g_ux) || !a8(g_uy) || !a8(g_T))
+    return LBM_EINVAL;
+  const StepArgs a = make_step_args(p);
+  return status_of(launch_init_adjoint(rho, ux, uy, T, (const double*)lam0, g_rho, g_ux, g_uy, g_T, a,
+                                       (cudaStream_t)stream));
+}
+
+}  // extern "C"

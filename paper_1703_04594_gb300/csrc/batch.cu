@@ -1,0 +1,450 @@
+// Batched stepping of many independent lattices of uneven sizes.
+//
+// Work unit: a chunk of `ny` consecutive warp-strips (32 rows each) of one column of one
+// lattice.  All lattices of a batch are laid end to end in one chunk index space (prefix
+// sums in BatchLattice::chunk_begin, y fastest inside a lattice); a warp finds its lattice
+// by binary search once per chunk and runs the same strip step as the single-lattice kernels (step_fp64.cuh / step_fp32.cuh) on each
+// strip of the chunk, so results are bit-identical to lbm_run per lattice.
+//
+// Modes:
+//   LBM_BATCH_PER_STEP   one launch per step over all strips of all lattices;
+//   LBM_BATCH_PERSISTENT one cooperative launch for all steps: warps stride over the
+//                        strips, and a grid barrier separates steps.  The barrier's wait is
+//                        bounded in time; on expiry it sets an error word, every block
+//                        returns, and lbm_batch_status reports LBM_ETIMEOUT.  Loads inside
+//                        this kernel bypass L1 (the sources were written by other SMs
+//                        earlier in the same launch);
+//   LBM_BATCH_LOOP       the plain single-lattice kernel launched per lattice per step
+//                        (the comparison baseline).
+// The autotuner times candidate (mode, warps per block, blocks per SM) on the batch itself
+// and keeps the fastest, in the spirit of the paper's start-up mini-benchmarks that pick
+// its tuning parameters (Sec. 6).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lbm_d2q37.h"
+#include "kernels.h"
+#include "step_fp32.cuh"
+
+namespace d2q37 {
+
+struct BatchLattice {
+  StepArgs a;
+  void* f[2];             // state buffers; f[parity] holds the current state
+  long long chunk_begin;  // first chunk of this lattice in the batch index space
+  int strips_y;           // ceil(ly / 32)
+  int chunks_y;           // ceil(strips_y / ny)
+};
+
+struct BatchSync {
+  unsigned int arrived;  // grid-barrier arrivals since the launch started
+  unsigned int error;    // 1 after a barrier wait expired
+  unsigned int step;     // step whose barrier expired
+  unsigned int pad;
+};
+
+namespace {
+
+__device__ __forceinline__ int find_lattice(const BatchLattice* __restrict__ L, int n, long long c) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L[mid].chunk_begin <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class T, bool PERIODIC, class Ld>
+__device__ __forceinline__ void batch_chunk(const BatchLattice* __restrict__ L, int n, long long c, int ny,
+                                            int parity, Ld ld) {
+  const int j = find_lattice(L, n, c);
+  const BatchLattice& B = L[j];
+  const long long local = c - B.chunk_begin;
+  const int x = (int)(local / B.chunks_y);
+  const int cy = (int)(local - (long long)x * B.chunks_y);
+  const int s_end = min((cy + 1) * ny, B.strips_y);
+  const T* src = (const T*)B.f[parity];
+  T* dst = (T*)B.f[parity ^ 1];
+#pragma unroll 1
+  for (int sy = cy * ny; sy < s_end; ++sy) {
+    if constexpr (sizeof(T) == 8) step_strip_fp64<PERIODIC>(src, dst, B.a, B.a, x, sy * 32, ld);
+    else step_strip_fp32<PERIODIC>(src, dst, B.a, B.a, x, sy * 32, ld);
+  }
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier with a bounded wait.  Returns false (for every thread of the block) when
+// the wait expired here or in another block.
+__device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, long long timeout_ns, int step) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&sync->arrived, 1u);
+    const unsigned long long t0 = global_ns();
+    const long long max_iter = timeout_ns / 64 + 4096;  // also bounded by iterations
+    long long it = 0;
+    int ok = 1;
+    while (ld_acquire_gpu(&sync->arrived) < target) {
+      if (ld_acquire_gpu(&sync->error) != 0u) {
+        ok = 0;
+        break;
+      }
+      if ((long long)(global_ns() - t0) > timeout_ns || ++it > max_iter) {
+        if (atomicCAS(&sync->error, 0u, 1u) == 0u) atomicExch(&sync->step, (unsigned)step);
+        ok = 0;
+        break;
+      }
+      __nanosleep(128);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace
+
+// Register cap: at most 256 threads per block (8 warps); the FP32 step keeps two such
+// blocks resident per SM (<= 128 registers), as the single-lattice FP32 kernel does.
+template <class T, bool PERIODIC>
+__global__ void __launch_bounds__(256) k_batch_step(const BatchLattice* __restrict__ L, int n, long long total, int ny, int parity) {
+  const int wpb = blockDim.x >> 5;
+  const long long c = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+  if (c >= total) return;  // uniform per warp
+  batch_chunk<T, PERIODIC>(L, n, c, ny, parity, LdReadOnly());
+}
+
+template <class T, bool PERIODIC>
+__global__ void __launch_bounds__(256) k_batch_persistent(const BatchLattice* __restrict__ L, int n, long long total, int ny, int parity0,
+                                   int steps, BatchSync* sync, unsigned phantom, long long timeout_ns) {
+  const int wpb = blockDim.x >> 5;
+  const long long nw = (long long)gridDim.x * wpb;
+  const long long w0 = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+  for (int st = 0; st < steps; ++st) {
+    const int parity = (parity0 + st) & 1;
+    for (long long c = w0; c < total; c += nw) batch_chunk<T, PERIODIC>(L, n, c, ny, parity, LdL2());
+    if (st + 1 < steps && !grid_barrier(sync, (unsigned)(st + 1) * gridDim.x + phantom, timeout_ns, st)) return;
+  }
+}
+
+}  // namespace d2q37
+
+using namespace d2q37;
+
+struct lbm_batch {
+  int n = 0;
+  int precision = LBM_FP64;
+  int periodic = 0;
+  long long total_chunks = 0;
+  int ny = 1;  // strips per chunk
+  std::vector<BatchLattice> host;
+  BatchLattice* dev_lattices = nullptr;
+  BatchSync* dev_sync = nullptr;
+  int parity = 0;
+  int mode = LBM_BATCH_PERSISTENT;
+  int warps_per_block = 4;
+  int blocks_per_sm = 0;  // 0 = as many as fit
+  long long timeout_ns = 2000000000LL;
+  unsigned phantom = 0;
+  int device = 0;
+  int sms = 0;
+};
+
+namespace {
+
+thread_local int32_t g_batch_cuda_error = 0;
+
+int32_t cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LBM_OK;
+  g_batch_cuda_error = (int32_t)e;
+  return LBM_ECUDA;
+}
+
+template <class T, bool P>
+void* persistent_fn() {
+  return (void*)k_batch_persistent<T, P>;
+}
+
+void* persistent_kernel(const lbm_batch* b) {
+  if (b->precision == LBM_FP64) return b->periodic ? persistent_fn<double, true>() : persistent_fn<double, false>();
+  return b->periodic ? persistent_fn<float, true>() : persistent_fn<float, false>();
+}
+
+int max_blocks_per_sm(const lbm_batch* b, int wpb) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel(b), 32 * wpb, 0) != cudaSuccess) return 0;
+  return nb;
+}
+
+int32_t launch_per_step(lbm_batch* b, int steps, cudaStream_t s) {
+  const int wpb = b->warps_per_block;
+  const long long blocks = (b->total_chunks + wpb - 1) / wpb;
+  if (blocks > 0x7fffffffLL) return LBM_EINVAL;
+  for (int st = 0; st < steps; ++st) {
+    const int par = (b->parity + st) & 1;
+    if (b->precision == LBM_FP64) {
+      if (b->periodic) k_batch_step<double, true><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
+      else k_batch_step<double, false><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
+    } else {
+      if (b->periodic) k_batch_step<float, true><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
+      else k_batch_step<float, false><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
+    }
+    const int32_t st_ = cuda_status(cudaGetLastError());
+    if (st_ != LBM_OK) return st_;
+  }
+  return LBM_OK;
+}
+
+int32_t launch_persistent(lbm_batch* b, int steps, cudaStream_t s) {
+  const int wpb = b->warps_per_block;
+  const int fit = max_blocks_per_sm(b, wpb);
+  if (fit <= 0) return LBM_EINVAL;
+  const int per_sm = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, fit) : fit;
+  const unsigned grid = (unsigned)(per_sm * b->sms);
+  if ((unsigned long long)steps * grid + b->phantom >= 0x7fffffffULL) return LBM_EINVAL;
+  int32_t st = cuda_status(cudaMemsetAsync(b->dev_sync, 0, sizeof(BatchSync), s));
+  if (st != LBM_OK) return st;
+  const BatchLattice* L = b->dev_lattices;
+  int n = b->n;
+  long long total = b->total_chunks;
+  int ny = b->ny;
+  int parity0 = b->parity;
+  BatchSync* sync = b->dev_sync;
+  unsigned phantom = b->phantom;
+  long long timeout = b->timeout_ns;
+  void* args[] = {(void*)&L, &n, &total, &ny, &parity0, &steps, &sync, &phantom, &timeout};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32 * wpb);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cuda_status(cudaLaunchKernelExC(&cfg, persistent_kernel(b), args));
+}
+
+int32_t launch_loop(lbm_batch* b, int steps, cudaStream_t s) {
+  for (int st = 0; st < steps; ++st) {
+    const int par = (b->parity + st) & 1;
+    for (int j = 0; j < b->n; ++j) {
+      const BatchLattice& B = b->host[j];
+      const int32_t r = cuda_status(launch_step(B.f[par], B.f[par ^ 1], B.a, b->precision, s));
+      if (r != LBM_OK) return r;
+    }
+  }
+  return LBM_OK;
+}
+
+int32_t run(lbm_batch* b, int steps, cudaStream_t s) {
+  if (steps <= 0) return steps == 0 ? LBM_OK : LBM_EINVAL;
+  int32_t st;
+  switch (b->mode) {
+    case LBM_BATCH_PER_STEP: st = launch_per_step(b, steps, s); break;
+    case LBM_BATCH_PERSISTENT: st = launch_persistent(b, steps, s); break;
+    case LBM_BATCH_LOOP: st = launch_loop(b, steps, s); break;
+    default: return LBM_EINVAL;
+  }
+  if (st == LBM_OK) b->parity ^= (steps & 1);
+  return st;
+}
+
+// Chunk layout for `ny` strips per chunk, uploaded to the device table (synchronous).
+int32_t relayout(lbm_batch* b, int ny) {
+  long long chunks = 0;
+  for (BatchLattice& L : b->host) {
+    L.chunks_y = (L.strips_y + ny - 1) / ny;
+    L.chunk_begin = chunks;
+    chunks += (long long)L.chunks_y * L.a.lx;
+  }
+  b->total_chunks = chunks;
+  b->ny = ny;
+  return cuda_status(cudaMemcpy(b->dev_lattices, b->host.data(), sizeof(BatchLattice) * b->n, cudaMemcpyHostToDevice));
+}
+
+bool overlap(const void* a, const void* b, int64_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + (uintptr_t)bytes && y < x + (uintptr_t)bytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* f_b, int32_t n, lbm_batch** out) {
+  if (!params || !f_a || !f_b || !out || n <= 0) return LBM_EINVAL;
+  *out = nullptr;
+  lbm_batch* b = new lbm_batch();
+  b->n = n;
+  b->precision = params[0].precision;
+  b->periodic = params[0].bc == LBM_BC_PERIODIC_Y;
+  for (int j = 0; j < n; ++j) {
+    const lbm_params* p = &params[j];
+    const int64_t bytes = lbm_buffer_bytes(p);
+    if (!params_valid(p) || p->precision != b->precision || p->bc != params[0].bc || bytes <= 0 || !f_a[j] ||
+        !f_b[j] || ((uintptr_t)f_a[j] % 16) || ((uintptr_t)f_b[j] % 16) || overlap(f_a[j], f_b[j], bytes)) {
+      delete b;
+      return LBM_EINVAL;
+    }
+    BatchLattice L;
+    memset(&L, 0, sizeof(L));
+    L.a = make_step_args(p);
+    L.f[0] = f_a[j];
+    L.f[1] = f_b[j];
+    L.strips_y = (p->ly + 31) / 32;
+    b->host.push_back(L);
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&b->device) != cudaSuccess || cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) {
+    delete b;
+    return LBM_ECUDA;
+  }
+  b->sms = prop.multiProcessorCount;
+  if (cudaMalloc(&b->dev_lattices, sizeof(BatchLattice) * n) != cudaSuccess) {
+    delete b;
+    return LBM_ENOMEM;
+  }
+  if (cudaMalloc(&b->dev_sync, sizeof(BatchSync)) != cudaSuccess) {
+    cudaFree(b->dev_lattices);
+    delete b;
+    return LBM_ENOMEM;
+  }
+  if (relayout(b, 1) != LBM_OK || cudaMemset(b->dev_sync, 0, sizeof(BatchSync)) != cudaSuccess) {
+    cudaFree(b->dev_lattices);
+    cudaFree(b->dev_sync);
+    delete b;
+    return LBM_ECUDA;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+int32_t lbm_batch_configure(lbm_batch* b, int32_t mode, int32_t warps_per_block, int32_t blocks_per_sm,
+                            int32_t strips_per_chunk) {
+  if (!b || (mode != LBM_BATCH_PER_STEP && mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_LOOP)) return LBM_EINVAL;
+  if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8) return LBM_EINVAL;
+  if (blocks_per_sm < 0 || blocks_per_sm > 64 || strips_per_chunk < 1 || strips_per_chunk > 64) return LBM_EINVAL;
+  b->mode = mode;
+  b->warps_per_block = warps_per_block;
+  b->blocks_per_sm = blocks_per_sm;
+  if (strips_per_chunk != b->ny) return relayout(b, strips_per_chunk);
+  return LBM_OK;
+}
+
+int32_t lbm_batch_config(const lbm_batch* b, int32_t* mode, int32_t* warps_per_block, int32_t* blocks_per_sm,
+                         int32_t* strips_per_chunk) {
+  if (!b) return LBM_EINVAL;
+  if (mode) *mode = b->mode;
+  if (warps_per_block) *warps_per_block = b->warps_per_block;
+  if (strips_per_chunk) *strips_per_chunk = b->ny;
+  if (blocks_per_sm) {
+    const int fit = b->mode == LBM_BATCH_PERSISTENT ? max_blocks_per_sm(b, b->warps_per_block) : 0;
+    *blocks_per_sm = b->mode == LBM_BATCH_PERSISTENT ? (b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, fit) : fit)
+                                                      : 0;
+  }
+  return LBM_OK;
+}
+
+int32_t lbm_batch_set_wait(lbm_batch* b, int64_t timeout_ns, int32_t phantom_arrivals) {
+  if (!b || timeout_ns <= 0 || timeout_ns > 60LL * 1000000000LL || phantom_arrivals < 0) return LBM_EINVAL;
+  b->timeout_ns = timeout_ns;
+  b->phantom = (unsigned)phantom_arrivals;
+  return LBM_OK;
+}
+
+int32_t lbm_batch_run(lbm_batch* b, int32_t n_steps, void* stream) {
+  if (!b || n_steps < 0) return LBM_EINVAL;
+  return run(b, n_steps, (cudaStream_t)stream);
+}
+
+int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream) {
+  if (!b || trial_steps < 1) return LBM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  struct Cand {
+    int mode, wpb, bps, ny;
+  };
+  std::vector<Cand> cands;
+  for (int ny : {1, 2, 4})
+    for (int wpb : {2, 4, 8}) cands.push_back({LBM_BATCH_PER_STEP, wpb, 0, ny});
+  for (int ny : {1, 4})
+    for (int wpb : {4, 8}) {
+      const int fit = max_blocks_per_sm(b, wpb);
+      for (int bps = fit; bps >= 1 && bps >= fit - 1; --bps) cands.push_back({LBM_BATCH_PERSISTENT, wpb, bps, ny});
+    }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LBM_ECUDA;
+  }
+  float best = 1e30f;
+  Cand best_c = {b->mode, b->warps_per_block, b->blocks_per_sm, b->ny};
+  int32_t st = LBM_OK;
+  for (const Cand& c : cands) {
+    if ((st = lbm_batch_configure(b, c.mode, c.wpb, c.bps, c.ny)) != LBM_OK) break;
+    if ((st = run(b, 1, s)) != LBM_OK) break;  // warm-up
+    cudaEventRecord(e0, s);
+    if ((st = run(b, trial_steps, s)) != LBM_OK) break;
+    cudaEventRecord(e1, s);
+    if ((st = cuda_status(cudaEventSynchronize(e1))) != LBM_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int32_t st2 = lbm_batch_configure(b, best_c.mode, best_c.wpb, best_c.bps, best_c.ny);
+  return st != LBM_OK ? st : st2;
+}
+
+int32_t lbm_batch_parity(const lbm_batch* b) { return b ? b->parity : -1; }
+
+int32_t lbm_batch_status(lbm_batch* b) {
+  if (!b) return LBM_EINVAL;
+  BatchSync h;
+  const int32_t st = cuda_status(cudaMemcpy(&h, b->dev_sync, sizeof(h), cudaMemcpyDeviceToHost));
+  if (st != LBM_OK) return st;
+  if (h.error) {
+    cudaMemset(b->dev_sync, 0, sizeof(BatchSync));
+    return LBM_ETIMEOUT;
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_batch_sites(const lbm_batch* b) {
+  if (!b) return -1;
+  int64_t s = 0;
+  for (const BatchLattice& L : b->host) s += (int64_t)L.a.lx * L.a.ly;
+  return s;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  cudaFree(b->dev_lattices);
+  cudaFree(b->dev_sync);
+  delete b;
+}
+
+}  // extern "C"

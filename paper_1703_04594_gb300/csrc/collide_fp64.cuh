@@ -12,7 +12,8 @@
 //     C0 = 1 - U/2 + t (q - D)/2 + U^2/8 + t U (D + 2 - q)/4 + t^2 (q^2 - 2(D+2) q + D(D+2))/8.
 // Work saved against the textbook form (Sec. 3 quotes ~7000 flops per site):
 //   * moments are sums over opposite pairs P = f_v + f_-v, M = f_v - f_-v with integer
-//     velocity weights grouped by value;
+//     velocity weights grouped by value, accumulated in 64-bit fixed point on the
+//     integer pipe;
 //   * C0..C2 are per shell (8 values of q), pre-multiplied by omega w_s rho;
 //   * each opposite pair shares the even part E(s^2) and odd part O(s):
 //     f_v^eq = E + O, f_-v^eq = E - O.
@@ -30,30 +31,62 @@ struct CollideConst {
 };
 
 // Moments in integer-velocity units: rho = sum f, (jx, jy) = sum v f, e = sum |v|^2 f.
+//
+// The sums run on the integer pipe, which is idle in this FP64-bound kernel: every f_i is
+// rounded to 64-bit fixed point with 2^-52 resolution (round to nearest),
+// the fixed-point sums are exact, and the four sums are converted back to float64.  The
+// error is at most 37 * 2^-53 absolute per moment, the same order as a float64
+// summation, and it is order-independent.  This takes 88 additions off the FP64 pipe.
+// Valid while sum_i |v_i|^2 |f_i| < 2048 (physical states: rho below ~200).
+constexpr int DFIX = 52;
+
+__device__ __forceinline__ long long to_fix52(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ffu);
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // 53-bit mantissa
+  const int sh = E - 1023;  // v * 2^52 = m * 2^sh
+  long long x;
+  if (sh >= 0) {
+    x = m << (sh < 10 ? sh : 10);
+  } else {
+    const int r = -sh;
+    x = r < 55 ? ((m + (1LL << (r - 1))) >> r) : 0;  // round half up in magnitude
+  }
+  x = E == 0 ? 0 : x;
+  const long long s = (long long)((long long)b >> 63);  // 0 or -1
+  return (x ^ s) - s;
+}
+
 __device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, double& jx, double& jy,
                                             double& e) {
-  double P[NPAIR + 1], M[NPAIR + 1];
+  long long X[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) X[i] = to_fix52(f[i]);
+  long long P[NPAIR + 1], M[NPAIR + 1];
 #pragma unroll
   for (int k = 1; k <= NPAIR; ++k) {
-    P[k] = f[k] + f[k + NPAIR];
-    M[k] = f[k] - f[k + NPAIR];
+    P[k] = X[k] + X[k + NPAIR];
+    M[k] = X[k] - X[k + NPAIR];
   }
   // shell sums of the pair sums (shells 1..7 hold |v|^2 = 1, 2, 4, 5, 8, 9, 10)
-  const double S1 = P[1] + P[2], S2 = P[3] + P[4], S3 = P[5] + P[6];
-  const double S4 = (P[7] + P[8]) + (P[9] + P[10]), S5 = P[11] + P[12], S6 = P[13] + P[14];
-  const double S7 = (P[15] + P[16]) + (P[17] + P[18]);
-  rho = ((f[0] + S1) + (S2 + S3)) + ((S4 + S5) + (S6 + S7));
-  e = fma(10.0, S7, fma(9.0, S6, fma(8.0, S5, fma(5.0, S4, fma(4.0, S3, fma(2.0, S2, S1))))));
+  const long long S1 = P[1] + P[2], S2 = P[3] + P[4], S3 = P[5] + P[6];
+  const long long S4 = P[7] + P[8] + P[9] + P[10], S5 = P[11] + P[12], S6 = P[13] + P[14];
+  const long long S7 = P[15] + P[16] + P[17] + P[18];
+  const long long R = X[0] + S1 + S2 + S3 + S4 + S5 + S6 + S7;
+  const long long Ei = S1 + 2 * S2 + 4 * S3 + 5 * S4 + 8 * S5 + 9 * S6 + 10 * S7;
   // x: vx = 1 for k in {1,3,4,8,10,16,18}, 2 for {5,7,9,11,12}, 3 for {13,15,17}
-  const double X1 = ((M[1] + M[3]) + (M[4] + M[8])) + ((M[10] + M[16]) + M[18]);
-  const double X2 = (M[5] + M[7]) + (M[9] + M[11]) + M[12];
-  const double X3 = (M[13] + M[15]) + M[17];
-  jx = fma(3.0, X3, fma(2.0, X2, X1));
+  const long long X1 = M[1] + M[3] + M[4] + M[8] + M[10] + M[16] + M[18];
+  const long long X2 = M[5] + M[7] + M[9] + M[11] + M[12];
+  const long long X3 = M[13] + M[15] + M[17];
   // y: vy = +1 {2,3,7,15}, -1 {4,9,17}, +2 {6,8,11}, -2 {10,12}, +3 {14,16}, -3 {18}
-  const double Y1 = ((M[2] + M[3]) + (M[7] + M[15])) - ((M[4] + M[9]) + M[17]);
-  const double Y2 = (M[6] + M[8]) + M[11] - (M[10] + M[12]);
-  const double Y3 = (M[14] + M[16]) - M[18];
-  jy = fma(3.0, Y3, fma(2.0, Y2, Y1));
+  const long long Y1 = (M[2] + M[3] + M[7] + M[15]) - (M[4] + M[9] + M[17]);
+  const long long Y2 = (M[6] + M[8] + M[11]) - (M[10] + M[12]);
+  const long long Y3 = (M[14] + M[16]) - M[18];
+  constexpr double S = 1.0 / 4503599627370496.0;  // 2^-52
+  rho = (double)R * S;
+  e = (double)Ei * S;
+  jx = (double)(X1 + 2 * X2 + 3 * X3) * S;
+  jy = (double)(Y1 + 2 * Y2 + 3 * Y3) * S;
 }
 
 // Equilibrium coefficients of one site.  R = omega * rho for a collision (the result is

@@ -1,27 +1,35 @@
 // Internal launch interface between the C-ABI layer (lbm_api.cu) and the kernels.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
+#include "../../include/lbm_d2q37.h"
 #include "collide_fp64.cuh"
 
 namespace d2q37 {
 
-// Everything a site kernel needs, passed by value as the kernel parameter.
-struct StepArgs {
+// Per-lattice scalars every site needs (small: kept in registers by the batched kernels).
+struct StepScalars {
   int lx, ly;
   long long pitch;      // elements per y-column
   long long pop;        // elements per population plane = lx * pitch
   int periodic;         // 1: y wraps (test mode), 0: thermal walls
   CollideConst cc;
+  double rho0;          // FP32 shifted storage: g_i = f_i - w_i rho0
+};
+
+// Wall tables, read only by the warps next to a wall.
+struct StepWalls {
   double wall_b[Q];     // w_i P_i(T_bottom): ghost value = rho_w * wall_b[i]
   double wall_t[Q];     // w_i P_i(T_top)
-  // FP32 shifted storage: g_i = f_i - w_i rho0
-  double rho0;
   float gb_scale[Q];    // ghost deviation = drho_w * gb_scale[i] + gb_bias[i]  (bottom wall)
   float gb_bias[Q];     //   with gb_scale = w_i P_i(T_b), gb_bias = w_i rho0 (P_i(T_b) - 1)
   float gt_scale[Q];    // same for the top wall
   float gt_bias[Q];
 };
+
+// Everything a site kernel needs, passed by value as the kernel parameter.
+struct StepArgs : StepScalars, StepWalls {};
 
 cudaError_t launch_step_fp64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_propagate_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s);
@@ -36,6 +44,11 @@ long long ke_partial_count(const StepArgs& a);
 cudaError_t launch_reduce_sum(const double* part, long long n, double* out, cudaStream_t s);
 cudaError_t launch_kinetic_energy_fp64(const double* f, double* out, double* part, const StepArgs& a,
                                        cudaStream_t s);
+
+// Parameter validation and launch arguments shared by the C-ABI files (lbm_api.cu).
+bool params_valid(const lbm_params* p);
+StepArgs make_step_args(const lbm_params* p);
+cudaError_t launch_step(const void* fin, void* fout, const StepArgs& a, int32_t precision, cudaStream_t s);
 
 // FP32 shifted-deviation storage
 cudaError_t launch_step_fp32(const float* fin, float* fout, const StepArgs& a, cudaStream_t s);

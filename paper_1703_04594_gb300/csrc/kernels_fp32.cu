@@ -1,220 +1,19 @@
-// FP32 shifted-deviation storage: the state holds g_i = f_i - w_i rho0 as float.
-//
-// Precision split (same step as the FP64 path: propagate -> bc -> collide, Sec. 5):
-//  * moments (eq. "macro") are accumulated in 64-bit fixed point with 2^-52 resolution:
-//    every stored float of magnitude >= 2^-29 converts exactly, the integer sums are
-//    exact and order-independent (error <= 37 * 2^-52 from the tiny values, the same
-//    order as a float64 accumulation), and the sums are then converted to float64;
-//  * density, energy and the temperature t = T_s - 1 (the equilibrium's temperature
-//    terms) are formed in float64 from those sums; 1/rho is a float32 seed refined by one
-//    float64 Newton step;
-//  * velocity, the Hermite coefficients and the BGK relaxation run in float32, written in
-//    deviation form  g_i' = (1 - 1/tau) g_i + (1/tau) (f_i^eq - w_i rho0),
-//    f_i^eq - w_i rho0 = w_i [ (rho - rho0) + rho (P_i(s) - 1) ],
-//    so float32 rounds deviations, not whole populations.
-// Valid range of the storage: |f_i - w_i rho0| < 16.
+// FP32 shifted-deviation storage kernels (step, init, moments, kinetic energy).
+// The precision split of the step is described in step_fp32.cuh.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "collide_fp64.cuh"
 #include "kernels.h"
+#include "step_fp32.cuh"
 
 namespace d2q37 {
-
-namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int FIX = 52;                                   // fixed-point fraction bits
-constexpr double FIX_SCALE = 1.0 / 4503599627370496.0;    // 2^-52
-constexpr float FIX_SCALE_F = 1.0f / 4503599627370496.0f;
-
-__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-// 32-bit shifts with PTX semantics: shift counts >= 32 give 0.
-__device__ __forceinline__ unsigned shl_clamp(unsigned x, unsigned s) {
-  unsigned r;
-  asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
-  return r;
-}
-__device__ __forceinline__ unsigned shr_clamp(unsigned x, unsigned s) {
-  unsigned r;
-  asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
-  return r;
-}
-
-// Float -> 64-bit fixed point (value * 2^52), exact for 2^-29 <= |v| < 16; smaller
-// magnitudes are truncated below 2^-52; zero and subnormals give 0.
-__device__ __forceinline__ long long to_fix(float v) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned m = (b & 0x7fffffu) | 0x800000u;
-  const int sh = (int)((b >> 23) & 0xffu) - (150 - FIX);  // v = m * 2^(e - 150)
-  unsigned lo, hi;
-  if (sh >= 0) {
-    lo = shl_clamp(m, (unsigned)sh);
-    hi = __funnelshift_lc(m, 0u, (unsigned)sh);
-  } else {
-    lo = shr_clamp(m, (unsigned)(-sh));
-    hi = 0u;
-  }
-  const long long x = (long long)(((unsigned long long)hi << 32) | lo);
-  const long long s = (long long)((int)b >> 31);  // 0 or -1
-  return (x ^ s) - s;
-}
-
-struct FixMoments {
-  long long drho, jx, jy, de;  // sum g, sum vx g, sum vy g, sum |v|^2 g  (all * 2^52)
-};
-
-__device__ __forceinline__ FixMoments moments_fix(const float (&g)[Q]) {
-  long long X[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) X[i] = to_fix(g[i]);
-  long long P[NPAIR + 1], M[NPAIR + 1];
-#pragma unroll
-  for (int k = 1; k <= NPAIR; ++k) {
-    P[k] = X[k] + X[k + NPAIR];
-    M[k] = X[k] - X[k + NPAIR];
-  }
-  const long long S1 = P[1] + P[2], S2 = P[3] + P[4], S3 = P[5] + P[6];
-  const long long S4 = P[7] + P[8] + P[9] + P[10], S5 = P[11] + P[12], S6 = P[13] + P[14];
-  const long long S7 = P[15] + P[16] + P[17] + P[18];
-  FixMoments r;
-  r.drho = X[0] + S1 + S2 + S3 + S4 + S5 + S6 + S7;
-  r.de = S1 + 2 * S2 + 4 * S3 + 5 * S4 + 8 * S5 + 9 * S6 + 10 * S7;
-  const long long X1 = M[1] + M[3] + M[4] + M[8] + M[10] + M[16] + M[18];
-  const long long X2 = M[5] + M[7] + M[9] + M[11] + M[12];
-  const long long X3 = M[13] + M[15] + M[17];
-  r.jx = X1 + 2 * X2 + 3 * X3;
-  const long long Y1 = (M[2] + M[3] + M[7] + M[15]) - (M[4] + M[9] + M[17]);
-  const long long Y2 = (M[6] + M[8] + M[11]) - (M[10] + M[12]);
-  const long long Y3 = (M[14] + M[16]) - M[18];
-  r.jy = Y1 + 2 * Y2 + 3 * Y3;
-  return r;
-}
-
-// Collision of one site in the precision split described at the top of the file.
-template <class Store>
-__device__ __forceinline__ void collide_site_fp32(const float (&g)[Q], const StepArgs& a, Store&& store) {
-  const FixMoments m = moments_fix(g);
-  // float64: density, energy, temperature
-  const double drho = (double)m.drho * FIX_SCALE;
-  const double rho = a.rho0 + drho;  // exact: power-of-two scale
-  const double etot = fma((double)m.de, FIX_SCALE, a.rho0 * (D / C2));  // sum |v|^2 f
-  const float rho_f = (float)rho;
-  const float r_f = __frcp_rn(rho_f);
-  const double r0 = (double)r_f;
-  const double inv = fma(r0, fma(-rho, r0, 1.0), r0);
-  // float32: velocity c u = c^2 j / rho
-  const float c2ir_f = (float)C2 * FIX_SCALE_F * r_f;
-  const float Ux0 = (float)m.jx * c2ir_f, Uy0 = (float)m.jy * c2ir_f;
-  const float uu = fmaf(Ux0, Ux0, Uy0 * Uy0) * (float)(1.0 / C2);
-  const double TD = fma(etot, C2 * inv, -(double)uu);                  // D T
-  const float t = (float)fma(TD, 1.0 / D, a.cc.tshift);                 // T_s - 1
-  const float drho_f = (float)drho;
-  // float32: Hermite coefficients in deviation form and relaxation
-  const float Ux = Ux0 + (float)a.cc.cgx, Uy = Uy0 + (float)a.cc.cgy;
-  const float U = fmaf(Ux, Ux, Uy * Uy) * (float)(1.0 / C2);
-  const float om = (float)a.cc.omega, om1 = (float)a.cc.om1;
-  const float tU = t * U, t2 = t * t;
-  const float a00m1 = fmaf(0.125f, U * U, fmaf(-0.5f, U, -t)) + (tU + t2);   // a00 - 1
-  const float a01 = fmaf(-0.25f, tU, 0.5f * t) - t2;
-  const float a02 = 0.125f * t2;
-  const float a10 = fmaf(-0.5f, U, 1.0f) - 2.0f * t;
-  const float a11 = 0.5f * t;
-  const float a20 = fmaf(-0.25f, U, 0.5f) - 1.5f * t;
-  const float a21 = 0.25f * t;
-  const float R = om * rho_f, Rd = om * drho_f;
-  float K0[8], K1[8], K2[8], K3[8], K4[8];
-  K0[0] = (float)w_shell(0) * fmaf(R, a00m1, Rd);
-#pragma unroll
-  for (int s = 1; s < 8; ++s) {
-    const float q = (float)q_shell(s);
-    const float ws = (float)w_shell(s);
-    const float W = R * ws;
-    K0[s] = fmaf(W, fmaf(fmaf(a02, q, a01), q, a00m1), Rd * ws);
-    K1[s] = W * fmaf(a11, q, a10);
-    K2[s] = W * fmaf(a21, q, a20);
-    K3[s] = W * (1.0f / 6.0f);
-    K4[s] = W * (1.0f / 24.0f);
-  }
-  float X[4] = {0.0f, Ux, Ux + Ux, 0.0f}, Y[4] = {0.0f, Uy, Uy + Uy, 0.0f};
-  X[3] = X[2] + Ux;
-  Y[3] = Y[2] + Uy;
-  store(0, fmaf(om1, g[0], K0[0]));
-#pragma unroll
-  for (int j = 1; j <= NPAIR; ++j) {
-    const int sh = shell(j), vxk = rep_vx(j), vyk = rep_vy(j);
-    float s;
-    if (vyk == 0) s = X[vxk];
-    else if (vxk == 0) s = Y[vyk];
-    else s = vyk > 0 ? X[vxk] + Y[vyk] : X[vxk] - Y[-vyk];
-    const float s2 = s * s;
-    const float E = fmaf(fmaf(K4[sh], s2, K2[sh]), s2, K0[sh]);
-    const float O = s * fmaf(K3[sh], s2, K1[sh]);
-    store(j, fmaf(om1, g[j], E + O));
-    store(j + NPAIR, fmaf(om1, g[j + NPAIR], E - O));
-  }
-}
-
-// Wall deviations sum_j g_j at (x_s, 0) and (x_s, ly-1) of the seven source columns
-// (lanes 0..6 bottom, 8..14 top), summed in float64, broadcast to the warp.
-__device__ __forceinline__ void wall_drho(const float* __restrict__ fin, int x, const StepArgs& a, float (&rb)[7],
-                                          float (&rt)[7]) {
-  const int lane = threadIdx.x & 31;
-  const int d = lane & 7;
-  const int row = lane < 8 ? 0 : a.ly - 1;
-  double r = 0.0;
-  if (d < 7 && lane < 16) {
-    const float* src = fin + (long long)wrap(x - (d - 3), a.lx) * a.pitch + row;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) r += (double)__ldg(src + i * a.pop);
-  }
-  const float rf = (float)r;
-#pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    rb[j] = __shfl_sync(FULL, rf, j);
-    rt[j] = __shfl_sync(FULL, rf, 8 + j);
-  }
-}
-
-}  // namespace
 
 template <bool PERIODIC>
 __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ fin, float* __restrict__ fout,
                                                    StepArgs a) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp
-  const int y0 = blockIdx.x * 32;
-  const int y = y0 + threadIdx.x;
-  const bool active = y < a.ly;
-  const int yc = active ? y : a.ly - 1;
-  long long col[7];
-#pragma unroll
-  for (int d = 0; d < 7; ++d) col[d] = (long long)wrap(x - (d - 3), a.lx) * a.pitch;
-  float g[Q];
-  const bool wall_warp = !PERIODIC && (y0 < 3 || y0 + 32 > a.ly - 3);
-  if (wall_warp) {
-    float rb[7], rt[7];
-    wall_drho(fin, x, a, rb, rt);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int ys = yc - vy(i);
-      const float* src = fin + i * a.pop + col[vx(i) + 3];
-      if (vy(i) > 0 && ys < 0) g[i] = fmaf(rb[vx(i) + 3], a.gb_scale[i], a.gb_bias[i]);
-      else if (vy(i) < 0 && ys >= a.ly) g[i] = fmaf(rt[vx(i) + 3], a.gt_scale[i], a.gt_bias[i]);
-      else g[i] = __ldg(src + ys);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      int ys = yc - vy(i);
-      if (PERIODIC) ys = wrap(ys, a.ly);
-      g[i] = __ldg(fin + i * a.pop + col[vx(i) + 3] + ys);
-    }
-  }
-  if (!active) return;
-  float* dst = fout + (long long)x * a.pitch + y;
-  collide_site_fp32(g, a, [&](int i, float v) { __stcs(dst + i * a.pop, v); });
+  step_strip_fp32<PERIODIC>(fin, fout, a, a, x, blockIdx.x * 32, LdReadOnly());
 }
 
 // g_i = f_i^eq(rho, u, T) - w_i rho0, equilibrium evaluated in float64 then rounded.
@@ -274,7 +73,7 @@ __global__ void __launch_bounds__(128) k_ke_partial_fp32(const float* __restrict
     ke = 0.5 * rho * fma(ux, ux, uy * uy);
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) ke += __shfl_down_sync(FULL, ke, off);
+  for (int off = 16; off > 0; off >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, off);
   __shared__ double warp_sum[4];
   if (threadIdx.x == 0) warp_sum[threadIdx.y] = ke;
   __syncthreads();

@@ -8,8 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "collide_fp64.cuh"
 #include "kernels.h"
+#include "step_fp64.cuh"
 
 namespace d2q37 {
 
@@ -17,7 +17,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__device__ __forceinline__ int wrap(int v, int n) { return wrap_index(v, n); }
 
 // Source column offsets x_s * pitch for hops vx = -3..3 (index vx + 3), x periodic.
 __device__ __forceinline__ void source_columns(int x, const StepArgs& a, long long (&col)[7]) {
@@ -25,81 +25,16 @@ __device__ __forceinline__ void source_columns(int x, const StepArgs& a, long lo
   for (int d = 0; d < 7; ++d) col[d] = (long long)wrap(x - (d - 3), a.lx) * a.pitch;
 }
 
-// Wall densities rho(x_s, 0) and rho(x_s, ly-1) of the seven source columns, computed by
-// lanes 0..6 (bottom) and 8..14 (top) of the warp and broadcast to all lanes.
-// Every lane of the warp must call this (it shuffles with the full mask).
-__device__ __forceinline__ void wall_densities(const double* __restrict__ fin, int x, const StepArgs& a,
-                                               double (&rb)[7], double (&rt)[7]) {
-  const int lane = threadIdx.x & 31;
-  const int d = lane & 7;
-  const int row = lane < 8 ? 0 : a.ly - 1;
-  double r = 0.0;
-  if (d < 7 && lane < 16) {
-    const double* src = fin + (long long)wrap(x - (d - 3), a.lx) * a.pitch + row;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) r += __ldg(src + i * a.pop);
-  }
-#pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    rb[j] = __shfl_sync(FULL, r, j);
-    rt[j] = __shfl_sync(FULL, r, 8 + j);
-  }
-}
-
-// Pull-gather of the 37 populations of site (x, yc) (Sec. 3, eq. "master2"), with the
-// thermal-wall values for sources outside the fluid.  WALL selects the slow path used by
-// warps within three rows of a wall.
-template <bool PERIODIC, bool WALL>
-__device__ __forceinline__ void gather(const double* __restrict__ fin, int yc, const long long (&col)[7],
-                                       const StepArgs& a, const double (&rb)[7], const double (&rt)[7],
-                                       double (&f)[Q]) {
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    int ys = yc - vy(i);
-    const double* src = fin + i * a.pop + col[vx(i) + 3];
-    if (PERIODIC) {
-      f[i] = __ldg(src + wrap(ys, a.ly));
-    } else if (!WALL) {
-      f[i] = __ldg(src + ys);
-    } else {
-      if (vy(i) > 0 && ys < 0) {
-        f[i] = rb[vx(i) + 3] * a.wall_b[i];
-      } else if (vy(i) < 0 && ys >= a.ly) {
-        f[i] = rt[vx(i) + 3] * a.wall_t[i];
-      } else {
-        f[i] = __ldg(src + ys);
-      }
-    }
-  }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
-// Fused step: gather (propagate + bc) -> collide -> streaming store.
+// Fused step: gather (propagate + bc) -> collide -> streaming store (step_fp64.cuh).
 template <bool PERIODIC>
 __global__ void __launch_bounds__(128) k_step_fp64(const double* __restrict__ fin, double* __restrict__ fout,
                                                    StepArgs a) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp
-  const int y0 = blockIdx.x * 32;
-  const int y = y0 + threadIdx.x;
-  const bool active = y < a.ly;
-  const int yc = active ? y : a.ly - 1;
-  long long col[7];
-  source_columns(x, a, col);
-  double f[Q];
-  double rb[7], rt[7];
-  const bool wall_warp = !PERIODIC && (y0 < 3 || y0 + 32 > a.ly - 3);
-  if (wall_warp) {
-    wall_densities(fin, x, a, rb, rt);
-    gather<PERIODIC, true>(fin, yc, col, a, rb, rt, f);
-  } else {
-    gather<PERIODIC, false>(fin, yc, col, a, rb, rt, f);
-  }
-  if (!active) return;
-  double* dst = fout + (long long)x * a.pitch + y;
-  collide_site(f, a.cc, [&](int i, double v) { __stcs(dst + i * a.pop, v); });
+  step_strip_fp64<PERIODIC>(fin, fout, a, a, x, blockIdx.x * 32, LdReadOnly());
 }
 
 // ---------------------------------------------------------------------------------------

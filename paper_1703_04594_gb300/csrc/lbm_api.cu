@@ -19,7 +19,9 @@ int32_t cuda_status(cudaError_t e) {
   return LBM_ECUDA;
 }
 
-bool params_ok(const lbm_params* p) {
+}  // namespace
+
+bool d2q37::params_valid(const lbm_params* p) {
   if (!p) return false;
   if (p->lx < 4 || p->ly < 6) return false;
   if (!(p->tau > 0.5) || !(p->tau < 1e6)) return false;
@@ -29,12 +31,18 @@ bool params_ok(const lbm_params* p) {
   if (p->lx > 4 * 65535) return false;
   const double sites = (double)p->lx * (double)p->ly;
   if (sites * Q > (double)(1LL << 40)) return false;
+  // one population plane (lx * pitch elements) must be addressable with 32-bit offsets
+  if ((double)p->lx * (double)(((int64_t)p->ly + 31) / 32 * 32) >= 4294967296.0) return false;
   const double vals[] = {p->gx, p->gy, p->t_bottom, p->t_top, p->rho0, p->tau};
   for (double v : vals)
     if (!(v == v) || v > 1e300 || v < -1e300) return false;  // NaN / inf
   if (!(p->t_bottom > 0) || !(p->t_top > 0)) return false;
   return true;
 }
+
+namespace {
+
+bool params_ok(const lbm_params* p) { return params_valid(p); }
 
 int64_t pitch_of(const lbm_params* p) { return ((int64_t)p->ly + 31) / 32 * 32; }
 int64_t elem_size(const lbm_params* p) { return p->precision == LBM_FP64 ? 8 : 4; }
@@ -55,7 +63,9 @@ double wall_multiplier(int i, double T) {
   return weight(i) * (1.0 + 0.5 * th * (q - D) + th * th * (q * q - 2.0 * (D + 2.0) * q + D * (D + 2.0)) / 8.0);
 }
 
-StepArgs make_args(const lbm_params* p) {
+}  // namespace
+
+StepArgs d2q37::make_step_args(const lbm_params* p) {
   StepArgs a;
   memset(&a, 0, sizeof(a));
   a.lx = p->lx;
@@ -81,12 +91,16 @@ StepArgs make_args(const lbm_params* p) {
   return a;
 }
 
-cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
-
-cudaError_t launch_step(const void* fin, void* fout, const StepArgs& a, int32_t precision, cudaStream_t s) {
+cudaError_t d2q37::launch_step(const void* fin, void* fout, const StepArgs& a, int32_t precision, cudaStream_t s) {
   if (precision == LBM_FP32_SHIFTED) return launch_step_fp32((const float*)fin, (float*)fout, a, s);
   return launch_step_fp64((const double*)fin, (double*)fout, a, s);
 }
+
+namespace {
+
+StepArgs make_args(const lbm_params* p) { return make_step_args(p); }
+
+cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
 }  // namespace
 

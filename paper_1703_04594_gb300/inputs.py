@@ -85,3 +85,14 @@ def rt_state(lx: int, ly: int, seed: int, t_bottom: float = 1.15, t_top: float =
     """Convenience: modes drawn from ``seed`` and the resulting fields."""
     modes = rt_modes(lx, ly, seed)
     return rt_fields(lx, ly, modes, t_bottom=t_bottom, t_top=t_top, g=g)
+
+
+def batch_workload(seed: int = 4, n: int = 256, sizes=tuple(range(128, 1025, 64)),
+                   tau_range=(0.6, 1.0)):
+    """Many independent Rayleigh-Taylor lattices of uneven sizes: for each lattice j,
+    Lx drawn from ``sizes`` (128, 192, ..., 1024), Ly = 2 Lx, tau ~ U[tau_range], and its
+    own interface seed.  Returns a list of (lx, ly, tau, interface_seed)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    lx = rng.choice(np.asarray(sizes), size=n)
+    tau = rng.uniform(tau_range[0], tau_range[1], size=n)
+    return [(int(a), int(2 * a), float(t), int(seed * 100000 + j)) for j, (a, t) in enumerate(zip(lx, tau))]

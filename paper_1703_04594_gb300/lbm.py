@@ -83,6 +83,20 @@ _SIGS = {
     "lbm_kinetic_energy_noalloc": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_simulate_host": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
                                            _VP, _VP, _VP, _VP]),
+    "lbm_adjoint_work_bytes": (ctypes.c_int64, [_PP]),
+    "lbm_adjoint_step": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "lbm_kinetic_energy_grad": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
+    "lbm_init_adjoint": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "lbm_batch_plan": (ctypes.c_int32, [_PP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_batch_configure": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_batch_config": (ctypes.c_int32, [_VP, _VP, _VP, _VP, _VP]),
+    "lbm_batch_autotune": (ctypes.c_int32, [_VP, ctypes.c_int32, _VP]),
+    "lbm_batch_run": (ctypes.c_int32, [_VP, ctypes.c_int32, _VP]),
+    "lbm_batch_parity": (ctypes.c_int32, [_VP]),
+    "lbm_batch_sites": (ctypes.c_int64, [_VP]),
+    "lbm_batch_status": (ctypes.c_int32, [_VP]),
+    "lbm_batch_set_wait": (ctypes.c_int32, [_VP, ctypes.c_int64, ctypes.c_int32]),
+    "lbm_batch_destroy": (None, [_VP]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
     "lbm_last_cuda_error": (ctypes.c_int32, []),
 }
@@ -267,3 +281,103 @@ def simulate_host(p: Params, fields_in, n_steps: int, fields_out, f_a, f_b, fiel
         ctypes.byref(p.c()), *fi, int(n_steps), *fo, _state(p, f_a, "f_a"), _state(p, f_b, "f_b"),
         _ptr(fields_dev), _stream(stream)))
     return fields_out
+
+
+# ------------------------------------------------------------------------- adjoint
+def adjoint_work(p: Params, device="cuda"):
+    n = _lib().lbm_adjoint_work_bytes(ctypes.byref(p.c()))
+    if n < 0:
+        raise LbmError("lbm_adjoint_work_bytes", EINVAL)
+    return torch.empty((n + 7) // 8, dtype=torch.float64, device=device)
+
+
+def adjoint_step(p: Params, f_n, lam_next, lam_n, dtau_acc, work, stream=None):
+    """lam_n = (d step/d f_n)^T lam_next; dtau_acc (0-d device float64) += dL/dtau part."""
+    _check("lbm_adjoint_step", _lib().lbm_adjoint_step(
+        ctypes.byref(p.c()), _state(p, f_n, "f_n"), _state(p, lam_next, "lam_next"), _state(p, lam_n, "lam_n"),
+        _ptr(dtau_acc), _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+    return lam_n
+
+
+def kinetic_energy_grad(p: Params, f, lam, stream=None):
+    _check("lbm_kinetic_energy_grad", _lib().lbm_kinetic_energy_grad(ctypes.byref(p.c()), _state(p, f, "f"),
+                                                                     _state(p, lam, "lam"), _stream(stream)))
+    return lam
+
+
+def init_adjoint(p: Params, rho, ux, uy, T, lam0, stream=None):
+    """(g_rho, g_ux, g_uy, g_T): gradients of the initial fields against lam0."""
+    out = [torch.empty((p.lx, p.ly), dtype=torch.float64, device=lam0.device) for _ in range(4)]
+    _check("lbm_init_adjoint", _lib().lbm_init_adjoint(
+        ctypes.byref(p.c()), _field(p, rho, "rho"), _field(p, ux, "ux"), _field(p, uy, "uy"), _field(p, T, "T"),
+        _state(p, lam0, "lam0"), *[_ptr(t) for t in out], _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------------- batched lattices
+BATCH_PER_STEP, BATCH_PERSISTENT, BATCH_LOOP = 1, 2, 3
+
+
+class Batch:
+    """Many independent lattices stepped together (C-ABI ``lbm_batch_*``).
+
+    ``params``: list of Params (same precision and bc); ``f_a`` / ``f_b``: matching lists of
+    state tensors (current state in ``f_a``).  The batch keeps the tensors alive.
+    """
+
+    def __init__(self, params, f_a, f_b):
+        if not (len(params) == len(f_a) == len(f_b) and len(params) > 0):
+            raise ValueError("params, f_a and f_b must be non-empty lists of equal length")
+        n = len(params)
+        self.params = list(params)
+        self.f = [list(f_a), list(f_b)]
+        arr = (CParams * n)(*[p.c() for p in params])
+        pa = (ctypes.c_void_p * n)(*[_state(p, t, "f_a").value for p, t in zip(params, f_a)])
+        pb = (ctypes.c_void_p * n)(*[_state(p, t, "f_b").value for p, t in zip(params, f_b)])
+        h = ctypes.c_void_p()
+        _check("lbm_batch_plan", _lib().lbm_batch_plan(arr, pa, pb, n, ctypes.byref(h)))
+        self._h = h
+
+    def configure(self, mode: int, warps_per_block: int = 4, blocks_per_sm: int = 0, strips_per_chunk: int = 1):
+        _check("lbm_batch_configure", _lib().lbm_batch_configure(self._h, mode, warps_per_block, blocks_per_sm,
+                                                                 strips_per_chunk))
+
+    def config(self):
+        m, w, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check("lbm_batch_config", _lib().lbm_batch_config(self._h, ctypes.byref(m), ctypes.byref(w),
+                                                           ctypes.byref(b), ctypes.byref(c)))
+        return {"mode": m.value, "warps_per_block": w.value, "blocks_per_sm": b.value, "strips_per_chunk": c.value}
+
+    def autotune(self, trial_steps: int = 3, stream=None):
+        _check("lbm_batch_autotune", _lib().lbm_batch_autotune(self._h, trial_steps, _stream(stream)))
+        return self.config()
+
+    def run(self, n_steps: int, stream=None):
+        _check("lbm_batch_run", _lib().lbm_batch_run(self._h, int(n_steps), _stream(stream)))
+
+    def parity(self) -> int:
+        return _lib().lbm_batch_parity(self._h)
+
+    def states(self):
+        """The tensors holding the current states."""
+        return self.f[self.parity()]
+
+    def sites(self) -> int:
+        return _lib().lbm_batch_sites(self._h)
+
+    def status(self) -> int:
+        return _lib().lbm_batch_status(self._h)
+
+    def set_wait(self, timeout_ns: int, phantom_arrivals: int = 0):
+        _check("lbm_batch_set_wait", _lib().lbm_batch_set_wait(self._h, int(timeout_ns), int(phantom_arrivals)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

