@@ -38,9 +38,10 @@ BYTES_PER_SITE_FP64 = 592          # 37 x 8 B read + 37 x 8 B written
 BYTES_PER_SITE_FP32 = 296          # 37 x 4 B read + 37 x 4 B written
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM bytes per launch of the fused FP64 step, from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on this workload; None until captured for the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None, "fp32": None}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture
+# of the current kernel on a smaller lattice, scaled to 4096 x 8192 by the site count;
+# profiles/ holds the captures).  None where no capture of the current kernel exists.
+TRAFFIC_BYTES_PER_LAUNCH = {"fused": 18.13e9, "separate": None, "fp32": 9.15e9}
 
 
 def _hbm_peak():
@@ -61,7 +62,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant", choices=["fused", "separate"], default="fused")
+    ap.add_argument("--variant", choices=["fused", "separate", "aos", "csoa"], default="fused",
+                    help="fused SoA step; separate propagate/bc/collide kernels; fused step in AoS or "
+                         "clustered-SoA layout (FP64)")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32 = FP32 shifted-deviation storage (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -78,6 +81,23 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(value: float, device="cpu") -> float:
+    """The largest value over all ranks (the slowest rank's time); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_mlups(sites_per_rank: int, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput: every rank's site updates over the slowest rank's time."""
+    return world * sites_per_rank * steps / (slowest_ms * 1e-3) / 1e6
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -198,10 +218,18 @@ def run_ours(a):
     ftmp = lbm.empty_state(p) if a.variant == "separate" else None
     lbm.init(p, *dev, fa)
     stream = torch.cuda.current_stream()
+    layout = {"aos": lbm.LAYOUT_AOS, "csoa": lbm.LAYOUT_CSOA}.get(a.variant)
+    if layout is not None:
+        if fp32:
+            raise SystemExit("layout variants run the FP64 step")
+        lbm.convert_layout(p, fa, lbm.LAYOUT_SOA, fb, layout, stream)
+        fa, fb = fb, fa
 
     def one_step(src, dst):
         if a.variant == "fused":
             lbm.step(p, src, dst, stream)
+        elif layout is not None:
+            lbm.step_layout(p, layout, src, dst, stream)
         else:
             lbm.propagate(p, src, ftmp, stream)
             lbm.bc(p, src, ftmp, stream)
@@ -226,13 +254,9 @@ def run_ours(a):
         dist.barrier()
     torch.cuda.synchronize()
     per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(a.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t)
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), "cuda")
     ms_per_step = total_ms / a.steps
-    value = world * sites * a.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_mlups(sites, a.steps, world, total_ms)
 
     # dominant kernel: the fused step is the only launch of a fused bench step
     kern_ms = statistics.mean(per_step)
@@ -244,8 +268,9 @@ def run_ours(a):
     else:
         achieved = FLOPS_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH[a.variant],
-                    "kernel": "k_step_fp64" if a.variant == "fused" else "whole step (3 kernels)",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(a.variant),
+                    "kernel": {"fused": "k_step_fp64", "separate": "whole step (3 kernels)",
+                               "aos": "k_step_layout<AoS>", "csoa": "k_step_layout<CSoA>"}[a.variant],
                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                     "hbm_gbs_equiv": BYTES_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e9}
 
@@ -259,13 +284,9 @@ def run_ours(a):
         dist.barrier()
     t0 = time.perf_counter()
     lbm.simulate_host(p, pinned_in, a.steps, pinned_out, fa, fb, fdev, stream)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
     field_bytes = 4 * sites * 8
-    e2e = {"value": world * sites * a.steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": whole_job_mlups(sites, a.steps, world, e2e_s * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": field_bytes / a.steps, "d2h_bytes_per_step": field_bytes / a.steps,
            "what": "lbm_simulate_host: fields H2D + init + K steps + moments + fields D2H, amortised per step"}
 
@@ -281,7 +302,7 @@ def run_ours(a):
                            "l2": "state buffers >= 4.9 GB >> 129 MB L2; no flush needed",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e,
-                "gpu_launches": a.steps * (1 if a.variant == "fused" else 3),
+                "gpu_launches": a.steps * (3 if a.variant == "separate" else 1),
                 "clocks": clk.summary()}
         if not a.no_cpu_baseline and world == 1 and (lx, ly) == (LX, LY):
             line["cpu_baseline"] = oracle_sample(4)
@@ -317,7 +338,7 @@ def run_batch(a):
         lbm.init(p, *dev, t)
     b.close()
     b = lbm.Batch(params, fa, fb)
-    b.configure(cfg["mode"], cfg["warps_per_block"], cfg["blocks_per_sm"], cfg["strips_per_chunk"])
+    b.configure(cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"])
     sites = b.sites()
     stream = torch.cuda.current_stream()
 
@@ -335,18 +356,22 @@ def run_batch(a):
         return e0.elapsed_time(e1)
 
     with ClockSampler(local) as clk:
-        ms = timed((cfg["mode"], cfg["warps_per_block"], cfg["blocks_per_sm"], cfg["strips_per_chunk"]), a.steps)
-    ms_loop = timed((lbm.BATCH_LOOP, 4, 0, 1), a.steps)
+        ms = timed((cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"]), a.steps)
+    ms_loop = timed((lbm.BATCH_LOOP, 4, 0), a.steps)
     value = sites * a.steps / (ms * 1e-3) / 1e6
     bytes_site = BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64
     if fp32:
         achieved = bytes_site * sites * a.steps / (ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": achieved / HBM_PEAK_GBS, "traffic": None, "kernel": "k_batch_persistent<float>"}
+                    "frac": achieved / HBM_PEAK_GBS, "traffic": None,
+                    "kernel": ("k_batch_persistent<float>" if cfg["mode"] == lbm.BATCH_PERSISTENT
+                               else "k_batch_step<float>")}
     else:
         achieved = FLOPS_PER_SITE_FP64 * sites * a.steps / (ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_batch_persistent<double>"}
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": ("k_batch_persistent<double>" if cfg["mode"] == lbm.BATCH_PERSISTENT
+                               else "k_batch_step<double>")}
     if rank == 0:
         line = {"metric": "D2Q37 MLUPS (batched)", "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,

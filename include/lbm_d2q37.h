@@ -144,6 +144,19 @@ int32_t lbm_simulate_host(const lbm_params* p, const double* rho_host, const dou
                           double* T_out_host, void* f_a_dev, void* f_b_dev, double* fields_dev,
                           void* stream);
 
+/* ---- Layout comparison (Sec. 4: AoS vs SoA vs clustered SoA), FP64 fused step, walls ----
+ * LBM_LAYOUT_SOA is the layout of every other entry point.  LBM_LAYOUT_AOS stores the 37
+ * populations of a site contiguously: element (i, x, y) at (x * pitch + y) * 37 + i.
+ * LBM_LAYOUT_CSOA splits each population column into 32 partitions of P = pitch / 32 rows
+ * and packs the k-th rows of the partitions into 32-wide clusters: element (i, x, y) at
+ * ((i * lx + x) * P + j) * 32 + k with y = k * P + j.  Same buffer size in every layout. */
+enum lbm_layout { LBM_LAYOUT_SOA = 0, LBM_LAYOUT_AOS = 1, LBM_LAYOUT_CSOA = 2 };
+/* dst = src re-laid out (SoA <-> AoS, SoA <-> CSoA); dst and src must not be the same. */
+int32_t lbm_convert_layout(const lbm_params* p, int32_t from, const void* src_dev, int32_t to, void* dst_dev,
+                           void* stream);
+/* One fused step of a state stored in layout AOS or CSOA (results bit-identical to lbm_step). */
+int32_t lbm_step_layout(const lbm_params* p, int32_t layout, const void* f_in_dev, void* f_out_dev, void* stream);
+
 /* ---- Adjoint (reverse mode) of the FP64 step, for gradients of observables ----
  * The paper steps forward only; these are the transposed Jacobians of the same operations
  * (propagate and bc are linear, collide is differentiated site by site through the
@@ -178,19 +191,17 @@ enum lbm_batch_mode {
 };
 /* Validates n lattices and binds their buffers (f_a_dev[j], f_b_dev[j]: device states of
  * lbm_buffer_bytes(&params[j]) bytes, current state in f_a).  Allocates the batch's own
- * device descriptor table and barrier word (the only allocating entry point; freed by
- * lbm_batch_destroy).  Synchronous.  Default configuration: persistent, 4 warps per block,
- * as many blocks per SM as fit, 1 strip per chunk. */
+ * device descriptor table, tile table and barrier word (the only allocating entry point; freed by
+ * lbm_batch_destroy).  Synchronous.  Default configuration: persistent, tiles of 32 x 4,
+ * as many blocks per SM as fit.  At most 65535 lattices. */
 int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a_dev, void* const* f_b_dev, int32_t n,
                        lbm_batch** out);
-/* Sets mode, warps per block (1, 2, 4, 8), blocks per SM (persistent only; 0 = all that fit)
- * and the tile shape: strips_per_chunk (1..64) consecutive 32-row strips of one column
- * handled by one warp per work item.  Synchronous when the tile shape changes. */
-int32_t lbm_batch_configure(lbm_batch* b, int32_t mode, int32_t warps_per_block, int32_t blocks_per_sm,
-                            int32_t strips_per_chunk);
+/* Sets mode, tile shape (a block steps a tile of 32 rows x tile_columns columns, one warp
+ * per column; tile_columns = 1, 2, 4 or 8) and blocks per SM (persistent only; 0 = all that
+ * fit).  Synchronous when the tile shape changes (the tile table is rebuilt). */
+int32_t lbm_batch_configure(lbm_batch* b, int32_t mode, int32_t tile_columns, int32_t blocks_per_sm);
 /* Reads the configuration (blocks_per_sm: the value the persistent launch uses, else 0). */
-int32_t lbm_batch_config(const lbm_batch* b, int32_t* mode, int32_t* warps_per_block, int32_t* blocks_per_sm,
-                         int32_t* strips_per_chunk);
+int32_t lbm_batch_config(const lbm_batch* b, int32_t* mode, int32_t* tile_columns, int32_t* blocks_per_sm);
 /* Times every candidate configuration for trial_steps steps (after one warm-up step each)
  * and keeps the fastest.  It ADVANCES the batch by (trial_steps + 1) steps per candidate:
  * call it before initialising the states, or on states whose evolution does not matter.

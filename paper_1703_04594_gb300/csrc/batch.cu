@@ -1,22 +1,24 @@
 // Batched stepping of many independent lattices of uneven sizes.
 //
-// Work unit: a chunk of `ny` consecutive warp-strips (32 rows each) of one column of one
-// lattice.  All lattices of a batch are laid end to end in one chunk index space (prefix
-// sums in BatchLattice::chunk_begin, y fastest inside a lattice); a warp finds its lattice
-// by binary search once per chunk and runs the same strip step as the single-lattice kernels (step_fp64.cuh / step_fp32.cuh) on each
-// strip of the chunk, so results are bit-identical to lbm_run per lattice.
+// Work unit: a tile of 32 rows x TX columns of one lattice, one warp per column, processed
+// by one block (TX = warps per block, the autotuned tile width).  All lattices of a batch
+// are laid end to end in one tile index space (prefix sums in BatchLattice::tile_begin, y
+// fastest inside a lattice) and a device table gives each tile's lattice, so everything a
+// block reads about its lattice is uniform across the block.  Each warp runs the same strip
+// step as the single-lattice kernels (step_fp64.cuh / step_fp32.cuh), so results are
+// bit-identical to lbm_run per lattice.
 //
 // Modes:
-//   LBM_BATCH_PER_STEP   one launch per step over all strips of all lattices;
-//   LBM_BATCH_PERSISTENT one cooperative launch for all steps: warps stride over the
-//                        strips, and a grid barrier separates steps.  The barrier's wait is
+//   LBM_BATCH_PER_STEP   one launch per step over all tiles of all lattices;
+//   LBM_BATCH_PERSISTENT one cooperative launch for all steps: blocks stride over the
+//                        tiles, and a grid barrier separates steps.  The barrier's wait is
 //                        bounded in time; on expiry it sets an error word, every block
 //                        returns, and lbm_batch_status reports LBM_ETIMEOUT.  Loads inside
 //                        this kernel bypass L1 (the sources were written by other SMs
 //                        earlier in the same launch);
 //   LBM_BATCH_LOOP       the plain single-lattice kernel launched per lattice per step
 //                        (the comparison baseline).
-// The autotuner times candidate (mode, warps per block, blocks per SM) on the batch itself
+// The autotuner times candidate (mode, tile width, blocks per SM) on the batch itself
 // and keeps the fastest, in the spirit of the paper's start-up mini-benchmarks that pick
 // its tuning parameters (Sec. 6).
 #include <cuda_runtime.h>
@@ -34,10 +36,10 @@ namespace d2q37 {
 
 struct BatchLattice {
   StepArgs a;
-  void* f[2];             // state buffers; f[parity] holds the current state
-  long long chunk_begin;  // first chunk of this lattice in the batch index space
-  int strips_y;           // ceil(ly / 32)
-  int chunks_y;           // ceil(strips_y / ny)
+  void* f[2];            // state buffers; f[parity] holds the current state
+  long long tile_begin;  // first tile of this lattice in the batch index space
+  int tiles_y;           // ceil(ly / 32)
+  int tiles_x;           // ceil(lx / TX)
 };
 
 struct BatchSync {
@@ -49,32 +51,23 @@ struct BatchSync {
 
 namespace {
 
-__device__ __forceinline__ int find_lattice(const BatchLattice* __restrict__ L, int n, long long c) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (L[mid].chunk_begin <= c) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
+// Tile t of the batch (32 rows x 4 columns, one warp per column, as the single-lattice
+// kernels): its lattice comes from a per-tile table, so everything that depends on the
+// lattice is uniform across the block.
 template <class T, bool PERIODIC, class Ld>
-__device__ __forceinline__ void batch_chunk(const BatchLattice* __restrict__ L, int n, long long c, int ny,
-                                            int parity, Ld ld) {
-  const int j = find_lattice(L, n, c);
+__device__ __forceinline__ void batch_tile(const BatchLattice* __restrict__ L, const unsigned short* __restrict__ tl,
+                                           long long t, int parity, Ld ld) {
+  const int j = tl[t];
   const BatchLattice& B = L[j];
-  const long long local = c - B.chunk_begin;
-  const int x = (int)(local / B.chunks_y);
-  const int cy = (int)(local - (long long)x * B.chunks_y);
-  const int s_end = min((cy + 1) * ny, B.strips_y);
+  const long long local = t - B.tile_begin;
+  const int tx = (int)(local / B.tiles_y);
+  const int ty = (int)(local - (long long)tx * B.tiles_y);
+  const int x = tx * (int)blockDim.y + (int)threadIdx.y;
+  if (x >= B.a.lx) return;  // uniform per warp
   const T* src = (const T*)B.f[parity];
   T* dst = (T*)B.f[parity ^ 1];
-#pragma unroll 1
-  for (int sy = cy * ny; sy < s_end; ++sy) {
-    if constexpr (sizeof(T) == 8) step_strip_fp64<PERIODIC>(src, dst, B.a, B.a, x, sy * 32, ld);
-    else step_strip_fp32<PERIODIC>(src, dst, B.a, B.a, x, sy * 32, ld);
-  }
+  if constexpr (sizeof(T) == 8) step_strip_fp64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
+  else step_strip_fp32<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
 }
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -94,7 +87,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, long long timeout_ns, int step) {
   __shared__ int s_ok;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
     __threadfence();
     atomicAdd(&sync->arrived, 1u);
     const unsigned long long t0 = global_ns();
@@ -124,22 +117,22 @@ __device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, l
 // Register cap: at most 256 threads per block (8 warps); the FP32 step keeps two such
 // blocks resident per SM (<= 128 registers), as the single-lattice FP32 kernel does.
 template <class T, bool PERIODIC>
-__global__ void __launch_bounds__(256) k_batch_step(const BatchLattice* __restrict__ L, int n, long long total, int ny, int parity) {
-  const int wpb = blockDim.x >> 5;
-  const long long c = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
-  if (c >= total) return;  // uniform per warp
-  batch_chunk<T, PERIODIC>(L, n, c, ny, parity, LdReadOnly());
+__global__ void __launch_bounds__(256) k_batch_step(const BatchLattice* __restrict__ L,
+                                                    const unsigned short* __restrict__ tl, long long total,
+                                                    int parity) {
+  const long long t = blockIdx.x;
+  if (t >= total) return;
+  batch_tile<T, PERIODIC>(L, tl, t, parity, LdReadOnly());
 }
 
 template <class T, bool PERIODIC>
-__global__ void __launch_bounds__(256) k_batch_persistent(const BatchLattice* __restrict__ L, int n, long long total, int ny, int parity0,
-                                   int steps, BatchSync* sync, unsigned phantom, long long timeout_ns) {
-  const int wpb = blockDim.x >> 5;
-  const long long nw = (long long)gridDim.x * wpb;
-  const long long w0 = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(256) k_batch_persistent(const BatchLattice* __restrict__ L,
+                                                          const unsigned short* __restrict__ tl, long long total,
+                                                          int parity0, int steps, BatchSync* sync, unsigned phantom,
+                                                          long long timeout_ns) {
   for (int st = 0; st < steps; ++st) {
     const int parity = (parity0 + st) & 1;
-    for (long long c = w0; c < total; c += nw) batch_chunk<T, PERIODIC>(L, n, c, ny, parity, LdL2());
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) batch_tile<T, PERIODIC>(L, tl, t, parity, LdL2());
     if (st + 1 < steps && !grid_barrier(sync, (unsigned)(st + 1) * gridDim.x + phantom, timeout_ns, st)) return;
   }
 }
@@ -152,14 +145,15 @@ struct lbm_batch {
   int n = 0;
   int precision = LBM_FP64;
   int periodic = 0;
-  long long total_chunks = 0;
-  int ny = 1;  // strips per chunk
+  long long total_tiles = 0;
+  unsigned short* dev_tile_lattice = nullptr;  // lattice of every tile
+  size_t tile_table_cap = 0;
   std::vector<BatchLattice> host;
   BatchLattice* dev_lattices = nullptr;
   BatchSync* dev_sync = nullptr;
   int parity = 0;
   int mode = LBM_BATCH_PERSISTENT;
-  int warps_per_block = 4;
+  int warps_per_block = 4;  // = tile width TX
   int blocks_per_sm = 0;  // 0 = as many as fit
   long long timeout_ns = 2000000000LL;
   unsigned phantom = 0;
@@ -193,18 +187,23 @@ int max_blocks_per_sm(const lbm_batch* b, int wpb) {
   return nb;
 }
 
+template <class T, bool P>
+void launch_step_kernel(const lbm_batch* b, int par, cudaStream_t s) {
+  const dim3 blk(32, b->warps_per_block);
+  k_batch_step<T, P><<<(unsigned)b->total_tiles, blk, 0, s>>>(b->dev_lattices, b->dev_tile_lattice, b->total_tiles,
+                                                              par);
+}
+
 int32_t launch_per_step(lbm_batch* b, int steps, cudaStream_t s) {
-  const int wpb = b->warps_per_block;
-  const long long blocks = (b->total_chunks + wpb - 1) / wpb;
-  if (blocks > 0x7fffffffLL) return LBM_EINVAL;
+  if (b->total_tiles > 0x7fffffffLL) return LBM_EINVAL;
   for (int st = 0; st < steps; ++st) {
     const int par = (b->parity + st) & 1;
     if (b->precision == LBM_FP64) {
-      if (b->periodic) k_batch_step<double, true><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
-      else k_batch_step<double, false><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
+      if (b->periodic) launch_step_kernel<double, true>(b, par, s);
+      else launch_step_kernel<double, false>(b, par, s);
     } else {
-      if (b->periodic) k_batch_step<float, true><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
-      else k_batch_step<float, false><<<(unsigned)blocks, 32 * wpb, 0, s>>>(b->dev_lattices, b->n, b->total_chunks, b->ny, par);
+      if (b->periodic) launch_step_kernel<float, true>(b, par, s);
+      else launch_step_kernel<float, false>(b, par, s);
     }
     const int32_t st_ = cuda_status(cudaGetLastError());
     if (st_ != LBM_OK) return st_;
@@ -222,17 +221,16 @@ int32_t launch_persistent(lbm_batch* b, int steps, cudaStream_t s) {
   int32_t st = cuda_status(cudaMemsetAsync(b->dev_sync, 0, sizeof(BatchSync), s));
   if (st != LBM_OK) return st;
   const BatchLattice* L = b->dev_lattices;
-  int n = b->n;
-  long long total = b->total_chunks;
-  int ny = b->ny;
+  const unsigned short* tl = b->dev_tile_lattice;
+  long long total = b->total_tiles;
   int parity0 = b->parity;
   BatchSync* sync = b->dev_sync;
   unsigned phantom = b->phantom;
   long long timeout = b->timeout_ns;
-  void* args[] = {(void*)&L, &n, &total, &ny, &parity0, &steps, &sync, &phantom, &timeout};
+  void* args[] = {(void*)&L, (void*)&tl, &total, &parity0, &steps, &sync, &phantom, &timeout};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(32 * wpb);
+  cfg.blockDim = dim3(32, wpb);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -268,16 +266,34 @@ int32_t run(lbm_batch* b, int steps, cudaStream_t s) {
   return st;
 }
 
-// Chunk layout for `ny` strips per chunk, uploaded to the device table (synchronous).
-int32_t relayout(lbm_batch* b, int ny) {
-  long long chunks = 0;
+// Tile layout for tiles of 32 rows x tx columns, and the per-tile lattice table, uploaded
+// to the device (synchronous; grows the table allocation when needed).
+int32_t relayout(lbm_batch* b, int tx) {
+  long long tiles = 0;
   for (BatchLattice& L : b->host) {
-    L.chunks_y = (L.strips_y + ny - 1) / ny;
-    L.chunk_begin = chunks;
-    chunks += (long long)L.chunks_y * L.a.lx;
+    L.tiles_y = (L.a.ly + 31) / 32;
+    L.tiles_x = (L.a.lx + tx - 1) / tx;
+    L.tile_begin = tiles;
+    tiles += (long long)L.tiles_y * L.tiles_x;
   }
-  b->total_chunks = chunks;
-  b->ny = ny;
+  std::vector<unsigned short> table((size_t)tiles);
+  for (int j = 0; j < b->n; ++j) {
+    const BatchLattice& L = b->host[j];
+    std::fill(table.begin() + L.tile_begin, table.begin() + L.tile_begin + (long long)L.tiles_y * L.tiles_x,
+              (unsigned short)j);
+  }
+  if ((size_t)tiles > b->tile_table_cap) {
+    if (b->dev_tile_lattice) cudaFree(b->dev_tile_lattice);
+    b->dev_tile_lattice = nullptr;
+    b->tile_table_cap = 0;
+    if (cudaMalloc(&b->dev_tile_lattice, sizeof(unsigned short) * (size_t)tiles) != cudaSuccess) return LBM_ENOMEM;
+    b->tile_table_cap = (size_t)tiles;
+  }
+  b->total_tiles = tiles;
+  b->warps_per_block = tx;
+  int32_t st = cuda_status(cudaMemcpy(b->dev_tile_lattice, table.data(), sizeof(unsigned short) * (size_t)tiles,
+                                      cudaMemcpyHostToDevice));
+  if (st != LBM_OK) return st;
   return cuda_status(cudaMemcpy(b->dev_lattices, b->host.data(), sizeof(BatchLattice) * b->n, cudaMemcpyHostToDevice));
 }
 
@@ -291,7 +307,7 @@ bool overlap(const void* a, const void* b, int64_t bytes) {
 extern "C" {
 
 int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* f_b, int32_t n, lbm_batch** out) {
-  if (!params || !f_a || !f_b || !out || n <= 0) return LBM_EINVAL;
+  if (!params || !f_a || !f_b || !out || n <= 0 || n > 65535) return LBM_EINVAL;
   *out = nullptr;
   lbm_batch* b = new lbm_batch();
   b->n = n;
@@ -310,7 +326,6 @@ int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* 
     L.a = make_step_args(p);
     L.f[0] = f_a[j];
     L.f[1] = f_b[j];
-    L.strips_y = (p->ly + 31) / 32;
     b->host.push_back(L);
   }
   cudaDeviceProp prop;
@@ -328,7 +343,8 @@ int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* 
     delete b;
     return LBM_ENOMEM;
   }
-  if (relayout(b, 1) != LBM_OK || cudaMemset(b->dev_sync, 0, sizeof(BatchSync)) != cudaSuccess) {
+  if (relayout(b, 4) != LBM_OK || cudaMemset(b->dev_sync, 0, sizeof(BatchSync)) != cudaSuccess) {
+    cudaFree(b->dev_tile_lattice);
     cudaFree(b->dev_lattices);
     cudaFree(b->dev_sync);
     delete b;
@@ -338,24 +354,20 @@ int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* 
   return LBM_OK;
 }
 
-int32_t lbm_batch_configure(lbm_batch* b, int32_t mode, int32_t warps_per_block, int32_t blocks_per_sm,
-                            int32_t strips_per_chunk) {
+int32_t lbm_batch_configure(lbm_batch* b, int32_t mode, int32_t tile_columns, int32_t blocks_per_sm) {
   if (!b || (mode != LBM_BATCH_PER_STEP && mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_LOOP)) return LBM_EINVAL;
-  if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8) return LBM_EINVAL;
-  if (blocks_per_sm < 0 || blocks_per_sm > 64 || strips_per_chunk < 1 || strips_per_chunk > 64) return LBM_EINVAL;
+  if (tile_columns != 1 && tile_columns != 2 && tile_columns != 4 && tile_columns != 8) return LBM_EINVAL;
+  if (blocks_per_sm < 0 || blocks_per_sm > 64) return LBM_EINVAL;
   b->mode = mode;
-  b->warps_per_block = warps_per_block;
   b->blocks_per_sm = blocks_per_sm;
-  if (strips_per_chunk != b->ny) return relayout(b, strips_per_chunk);
+  if (tile_columns != b->warps_per_block) return relayout(b, tile_columns);
   return LBM_OK;
 }
 
-int32_t lbm_batch_config(const lbm_batch* b, int32_t* mode, int32_t* warps_per_block, int32_t* blocks_per_sm,
-                         int32_t* strips_per_chunk) {
+int32_t lbm_batch_config(const lbm_batch* b, int32_t* mode, int32_t* tile_columns, int32_t* blocks_per_sm) {
   if (!b) return LBM_EINVAL;
   if (mode) *mode = b->mode;
-  if (warps_per_block) *warps_per_block = b->warps_per_block;
-  if (strips_per_chunk) *strips_per_chunk = b->ny;
+  if (tile_columns) *tile_columns = b->warps_per_block;
   if (blocks_per_sm) {
     const int fit = b->mode == LBM_BATCH_PERSISTENT ? max_blocks_per_sm(b, b->warps_per_block) : 0;
     *blocks_per_sm = b->mode == LBM_BATCH_PERSISTENT ? (b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, fit) : fit)
@@ -380,16 +392,14 @@ int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream) {
   if (!b || trial_steps < 1) return LBM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   struct Cand {
-    int mode, wpb, bps, ny;
+    int mode, tx, bps;
   };
   std::vector<Cand> cands;
-  for (int ny : {1, 2, 4})
-    for (int wpb : {2, 4, 8}) cands.push_back({LBM_BATCH_PER_STEP, wpb, 0, ny});
-  for (int ny : {1, 4})
-    for (int wpb : {4, 8}) {
-      const int fit = max_blocks_per_sm(b, wpb);
-      for (int bps = fit; bps >= 1 && bps >= fit - 1; --bps) cands.push_back({LBM_BATCH_PERSISTENT, wpb, bps, ny});
-    }
+  for (int tx : {2, 4, 8}) cands.push_back({LBM_BATCH_PER_STEP, tx, 0});
+  for (int tx : {2, 4, 8}) {
+    const int fit = max_blocks_per_sm(b, tx);
+    for (int bps = fit; bps >= 1 && bps >= fit - 1; --bps) cands.push_back({LBM_BATCH_PERSISTENT, tx, bps});
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -397,10 +407,10 @@ int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream) {
     return LBM_ECUDA;
   }
   float best = 1e30f;
-  Cand best_c = {b->mode, b->warps_per_block, b->blocks_per_sm, b->ny};
+  Cand best_c = {b->mode, b->warps_per_block, b->blocks_per_sm};
   int32_t st = LBM_OK;
   for (const Cand& c : cands) {
-    if ((st = lbm_batch_configure(b, c.mode, c.wpb, c.bps, c.ny)) != LBM_OK) break;
+    if ((st = lbm_batch_configure(b, c.mode, c.tx, c.bps)) != LBM_OK) break;
     if ((st = run(b, 1, s)) != LBM_OK) break;  // warm-up
     cudaEventRecord(e0, s);
     if ((st = run(b, trial_steps, s)) != LBM_OK) break;
@@ -415,7 +425,7 @@ int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  const int32_t st2 = lbm_batch_configure(b, best_c.mode, best_c.wpb, best_c.bps, best_c.ny);
+  const int32_t st2 = lbm_batch_configure(b, best_c.mode, best_c.tx, best_c.bps);
   return st != LBM_OK ? st : st2;
 }
 
@@ -442,6 +452,7 @@ int64_t lbm_batch_sites(const lbm_batch* b) {
 
 void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
+  cudaFree(b->dev_tile_lattice);
   cudaFree(b->dev_lattices);
   cudaFree(b->dev_sync);
   delete b;

@@ -45,48 +45,35 @@ __device__ __forceinline__ long long to_fix52(double v) {
   const int E = (int)((b >> 52) & 0x7ffu);
   const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // 53-bit mantissa
   const int sh = E - 1023;  // v * 2^52 = m * 2^sh
-  long long x;
-  if (sh >= 0) {
-    x = m << (sh < 10 ? sh : 10);
-  } else {
-    const int r = -sh;
-    x = r < 55 ? ((m + (1LL << (r - 1))) >> r) : 0;  // round half up in magnitude
-  }
+  const int l = sh < 0 ? 0 : (sh < 10 ? sh : 10);   // left shift (|v| >= 1)
+  const int r = sh < 0 ? (-sh < 55 ? -sh : 55) : 0;  // right shift (|v| < 1), rounded
+  const long long half = r > 0 ? (1LL << (r - 1)) : 0;
+  long long x = ((m + half) >> r) << l;
   x = E == 0 ? 0 : x;
   const long long s = (long long)((long long)b >> 63);  // 0 or -1
   return (x ^ s) - s;
 }
 
+// Streaming accumulation: each opposite pair is converted and added to the four sums
+// at once, so only the sums stay live (the products by the small integer velocity
+// weights are exact integer shifts and adds).
 __device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, double& jx, double& jy,
                                             double& e) {
-  long long X[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) X[i] = to_fix52(f[i]);
-  long long P[NPAIR + 1], M[NPAIR + 1];
+  long long R = to_fix52(f[0]), Ei = 0, Jx = 0, Jy = 0;
 #pragma unroll
   for (int k = 1; k <= NPAIR; ++k) {
-    P[k] = X[k] + X[k + NPAIR];
-    M[k] = X[k] - X[k + NPAIR];
+    const long long a = to_fix52(f[k]), b = to_fix52(f[k + NPAIR]);
+    const long long P = a + b, M = a - b;
+    R += P;
+    Ei += (long long)v2(k) * P;
+    if (rep_vx(k) != 0) Jx += (long long)rep_vx(k) * M;
+    if (rep_vy(k) != 0) Jy += (long long)rep_vy(k) * M;
   }
-  // shell sums of the pair sums (shells 1..7 hold |v|^2 = 1, 2, 4, 5, 8, 9, 10)
-  const long long S1 = P[1] + P[2], S2 = P[3] + P[4], S3 = P[5] + P[6];
-  const long long S4 = P[7] + P[8] + P[9] + P[10], S5 = P[11] + P[12], S6 = P[13] + P[14];
-  const long long S7 = P[15] + P[16] + P[17] + P[18];
-  const long long R = X[0] + S1 + S2 + S3 + S4 + S5 + S6 + S7;
-  const long long Ei = S1 + 2 * S2 + 4 * S3 + 5 * S4 + 8 * S5 + 9 * S6 + 10 * S7;
-  // x: vx = 1 for k in {1,3,4,8,10,16,18}, 2 for {5,7,9,11,12}, 3 for {13,15,17}
-  const long long X1 = M[1] + M[3] + M[4] + M[8] + M[10] + M[16] + M[18];
-  const long long X2 = M[5] + M[7] + M[9] + M[11] + M[12];
-  const long long X3 = M[13] + M[15] + M[17];
-  // y: vy = +1 {2,3,7,15}, -1 {4,9,17}, +2 {6,8,11}, -2 {10,12}, +3 {14,16}, -3 {18}
-  const long long Y1 = (M[2] + M[3] + M[7] + M[15]) - (M[4] + M[9] + M[17]);
-  const long long Y2 = (M[6] + M[8] + M[11]) - (M[10] + M[12]);
-  const long long Y3 = (M[14] + M[16]) - M[18];
   constexpr double S = 1.0 / 4503599627370496.0;  // 2^-52
   rho = (double)R * S;
   e = (double)Ei * S;
-  jx = (double)(X1 + 2 * X2 + 3 * X3) * S;
-  jy = (double)(Y1 + 2 * Y2 + 3 * Y3) * S;
+  jx = (double)Jx * S;
+  jy = (double)Jy * S;
 }
 
 // Equilibrium coefficients of one site.  R = omega * rho for a collision (the result is

@@ -16,6 +16,7 @@ struct StepScalars {
   int periodic;         // 1: y wraps (test mode), 0: thermal walls
   CollideConst cc;
   double rho0;          // FP32 shifted storage: g_i = f_i - w_i rho0
+  float f_omega, f_om1, f_cgx, f_cgy;  // float copies of cc for the FP32 collision
 };
 
 // Wall tables, read only by the warps next to a wall.

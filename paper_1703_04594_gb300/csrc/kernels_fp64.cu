@@ -30,7 +30,7 @@ __device__ __forceinline__ void source_columns(int x, const StepArgs& a, long lo
 // ---------------------------------------------------------------------------------------
 // Fused step: gather (propagate + bc) -> collide -> streaming store (step_fp64.cuh).
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128) k_step_fp64(const double* __restrict__ fin, double* __restrict__ fout,
+__global__ void __launch_bounds__(128, 4) k_step_fp64(const double* __restrict__ fin, double* __restrict__ fout,
                                                    StepArgs a) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp

@@ -80,6 +80,10 @@ StepArgs d2q37::make_step_args(const lbm_params* p) {
   a.cc.cgy = C * tau * p->gy;
   a.cc.tshift = tau * (1.0 - tau) * (p->gx * p->gx + p->gy * p->gy) / D - 1.0;
   a.rho0 = p->rho0;
+  a.f_omega = (float)a.cc.omega;
+  a.f_om1 = (float)a.cc.om1;
+  a.f_cgx = (float)a.cc.cgx;
+  a.f_cgy = (float)a.cc.cgy;
   for (int i = 0; i < Q; ++i) {
     a.wall_b[i] = wall_multiplier(i, p->t_bottom);
     a.wall_t[i] = wall_multiplier(i, p->t_top);

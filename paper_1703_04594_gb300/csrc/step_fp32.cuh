@@ -59,29 +59,21 @@ struct FixMoments {
 };
 
 __device__ __forceinline__ FixMoments moments_fix(const float (&g)[Q]) {
-  long long X[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) X[i] = to_fix(g[i]);
-  long long P[NPAIR + 1], M[NPAIR + 1];
+  // streaming: each opposite pair is converted and added to the four sums at once
+  FixMoments r;
+  r.drho = to_fix(g[0]);
+  r.de = 0;
+  r.jx = 0;
+  r.jy = 0;
 #pragma unroll
   for (int k = 1; k <= NPAIR; ++k) {
-    P[k] = X[k] + X[k + NPAIR];
-    M[k] = X[k] - X[k + NPAIR];
+    const long long a = to_fix(g[k]), b = to_fix(g[k + NPAIR]);
+    const long long P = a + b, M = a - b;
+    r.drho += P;
+    r.de += (long long)v2(k) * P;
+    if (rep_vx(k) != 0) r.jx += (long long)rep_vx(k) * M;
+    if (rep_vy(k) != 0) r.jy += (long long)rep_vy(k) * M;
   }
-  const long long S1 = P[1] + P[2], S2 = P[3] + P[4], S3 = P[5] + P[6];
-  const long long S4 = P[7] + P[8] + P[9] + P[10], S5 = P[11] + P[12], S6 = P[13] + P[14];
-  const long long S7 = P[15] + P[16] + P[17] + P[18];
-  FixMoments r;
-  r.drho = X[0] + S1 + S2 + S3 + S4 + S5 + S6 + S7;
-  r.de = S1 + 2 * S2 + 4 * S3 + 5 * S4 + 8 * S5 + 9 * S6 + 10 * S7;
-  const long long X1 = M[1] + M[3] + M[4] + M[8] + M[10] + M[16] + M[18];
-  const long long X2 = M[5] + M[7] + M[9] + M[11] + M[12];
-  const long long X3 = M[13] + M[15] + M[17];
-  r.jx = X1 + 2 * X2 + 3 * X3;
-  const long long Y1 = (M[2] + M[3] + M[7] + M[15]) - (M[4] + M[9] + M[17]);
-  const long long Y2 = (M[6] + M[8] + M[11]) - (M[10] + M[12]);
-  const long long Y3 = (M[14] + M[16]) - M[18];
-  r.jy = Y1 + 2 * Y2 + 3 * Y3;
   return r;
 }
 
@@ -101,13 +93,14 @@ __device__ __forceinline__ void collide_site_fp32(const float (&g)[Q], const Ste
   const float c2ir_f = (float)C2 * FIX_SCALE_F * r_f;
   const float Ux0 = (float)m.jx * c2ir_f, Uy0 = (float)m.jy * c2ir_f;
   const float uu = fmaf(Ux0, Ux0, Uy0 * Uy0) * (float)(1.0 / C2);
-  const double TD = fma(etot, C2 * inv, -(double)uu);                  // D T
-  const float t = (float)fma(TD, 1.0 / D, a.cc.tshift);                 // T_s - 1
+  // t = T_s - 1 = (c^2 e / rho - |u|^2) / D + tau (1 - tau) |g|^2 / D - 1: the large part in
+  // float64, the small |u|^2 / D correction in float32
+  const float t = (float)fma(etot, C2 * inv * (1.0 / D), a.cc.tshift) - uu * (float)(1.0 / D);
   const float drho_f = (float)drho;
   // float32: Hermite coefficients in deviation form and relaxation
-  const float Ux = Ux0 + (float)a.cc.cgx, Uy = Uy0 + (float)a.cc.cgy;
+  const float Ux = Ux0 + a.f_cgx, Uy = Uy0 + a.f_cgy;
   const float U = fmaf(Ux, Ux, Uy * Uy) * (float)(1.0 / C2);
-  const float om = (float)a.cc.omega, om1 = (float)a.cc.om1;
+  const float om = a.f_omega, om1 = a.f_om1;
   const float tU = t * U, t2 = t * t;
   const float a00m1 = fmaf(0.125f, U * U, fmaf(-0.5f, U, -t)) + (tU + t2);   // a00 - 1
   const float a01 = fmaf(-0.25f, tU, 0.5f * t) - t2;

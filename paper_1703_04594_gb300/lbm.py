@@ -83,13 +83,15 @@ _SIGS = {
     "lbm_kinetic_energy_noalloc": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_simulate_host": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
                                            _VP, _VP, _VP, _VP]),
+    "lbm_convert_layout": (ctypes.c_int32, [_PP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, _VP]),
+    "lbm_step_layout": (ctypes.c_int32, [_PP, ctypes.c_int32, _VP, _VP, _VP]),
     "lbm_adjoint_work_bytes": (ctypes.c_int64, [_PP]),
     "lbm_adjoint_step": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "lbm_kinetic_energy_grad": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_init_adjoint": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "lbm_batch_plan": (ctypes.c_int32, [_PP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
-    "lbm_batch_configure": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
-    "lbm_batch_config": (ctypes.c_int32, [_VP, _VP, _VP, _VP, _VP]),
+    "lbm_batch_configure": (ctypes.c_int32, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_batch_config": (ctypes.c_int32, [_VP, _VP, _VP, _VP]),
     "lbm_batch_autotune": (ctypes.c_int32, [_VP, ctypes.c_int32, _VP]),
     "lbm_batch_run": (ctypes.c_int32, [_VP, ctypes.c_int32, _VP]),
     "lbm_batch_parity": (ctypes.c_int32, [_VP]),
@@ -283,6 +285,22 @@ def simulate_host(p: Params, fields_in, n_steps: int, fields_out, f_a, f_b, fiel
     return fields_out
 
 
+# ------------------------------------------------------------------------- layouts
+LAYOUT_SOA, LAYOUT_AOS, LAYOUT_CSOA = 0, 1, 2
+
+
+def convert_layout(p: Params, src, frm: int, dst, to: int, stream=None):
+    _check("lbm_convert_layout", _lib().lbm_convert_layout(ctypes.byref(p.c()), frm, _state(p, src, "src"), to,
+                                                           _state(p, dst, "dst"), _stream(stream)))
+    return dst
+
+
+def step_layout(p: Params, layout: int, f_in, f_out, stream=None):
+    _check("lbm_step_layout", _lib().lbm_step_layout(ctypes.byref(p.c()), layout, _state(p, f_in, "f_in"),
+                                                     _state(p, f_out, "f_out"), _stream(stream)))
+    return f_out
+
+
 # ------------------------------------------------------------------------- adjoint
 def adjoint_work(p: Params, device="cuda"):
     n = _lib().lbm_adjoint_work_bytes(ctypes.byref(p.c()))
@@ -338,15 +356,14 @@ class Batch:
         _check("lbm_batch_plan", _lib().lbm_batch_plan(arr, pa, pb, n, ctypes.byref(h)))
         self._h = h
 
-    def configure(self, mode: int, warps_per_block: int = 4, blocks_per_sm: int = 0, strips_per_chunk: int = 1):
-        _check("lbm_batch_configure", _lib().lbm_batch_configure(self._h, mode, warps_per_block, blocks_per_sm,
-                                                                 strips_per_chunk))
+    def configure(self, mode: int, tile_columns: int = 4, blocks_per_sm: int = 0):
+        _check("lbm_batch_configure", _lib().lbm_batch_configure(self._h, mode, tile_columns, blocks_per_sm))
 
     def config(self):
-        m, w, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        m, w, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check("lbm_batch_config", _lib().lbm_batch_config(self._h, ctypes.byref(m), ctypes.byref(w),
-                                                           ctypes.byref(b), ctypes.byref(c)))
-        return {"mode": m.value, "warps_per_block": w.value, "blocks_per_sm": b.value, "strips_per_chunk": c.value}
+                                                           ctypes.byref(b)))
+        return {"mode": m.value, "tile_columns": w.value, "blocks_per_sm": b.value}
 
     def autotune(self, trial_steps: int = 3, stream=None):
         _check("lbm_batch_autotune", _lib().lbm_batch_autotune(self._h, trial_steps, _stream(stream)))

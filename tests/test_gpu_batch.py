@@ -49,14 +49,13 @@ def assert_equal_states(params, got, want):
 
 
 @pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_SHIFTED])
-@pytest.mark.parametrize("mode,wpb,ny", [(lbm.BATCH_PER_STEP, 4, 1), (lbm.BATCH_PER_STEP, 2, 3),
-                                         (lbm.BATCH_PERSISTENT, 4, 1), (lbm.BATCH_PERSISTENT, 8, 4),
-                                         (lbm.BATCH_LOOP, 4, 1)])
-def test_batch_equals_single_lattice_runs(precision, mode, wpb, ny):
+@pytest.mark.parametrize("mode,tx", [(lbm.BATCH_PER_STEP, 4), (lbm.BATCH_PER_STEP, 1), (lbm.BATCH_PER_STEP, 8),
+                                      (lbm.BATCH_PERSISTENT, 4), (lbm.BATCH_PERSISTENT, 2), (lbm.BATCH_LOOP, 4)])
+def test_batch_equals_single_lattice_runs(precision, mode, tx):
     params, fa, fb = make_batch(precision)
     want = reference(params, fa, 5)
     b = lbm.Batch(params, fa, fb)
-    b.configure(mode, wpb, 0, ny)
+    b.configure(mode, tx, 0)
     b.run(2)
     b.run(3)                      # parity carried across runs
     torch.cuda.synchronize()
@@ -81,12 +80,12 @@ def test_autotune_then_correct_run():
     b = lbm.Batch(params, fa, fb)
     cfg = b.autotune(trial_steps=2)          # advances the (throw-away) states
     assert cfg["mode"] in (lbm.BATCH_PER_STEP, lbm.BATCH_PERSISTENT)
-    assert cfg["warps_per_block"] in (2, 4, 8)
+    assert cfg["tile_columns"] in (2, 4, 8)
     b.close()
     params, fa, fb = make_batch(lbm.FP32_SHIFTED, seed0=200)
     want = reference(params, fa, 6)
     b = lbm.Batch(params, fa, fb)
-    b.configure(cfg["mode"], cfg["warps_per_block"], cfg["blocks_per_sm"], cfg["strips_per_chunk"])
+    b.configure(cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"])
     b.run(6)
     assert_equal_states(params, b.states(), want)
     b.close()
