@@ -68,8 +68,9 @@ def _args():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32 = FP32 shifted-deviation storage (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batch"], default="single",
-                    help="batch = 256 independent lattices of uneven sizes (persistent launch)")
+    ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
+                    help="batch = 256 independent lattices of uneven sizes; adjoint = gradient of the "
+                         "kinetic energy after 500 steps of a 512x1024 lattice (checkpoints every 22)")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--lx", type=int, default=LX, help="lattice width (profiling of smaller cases)")
     ap.add_argument("--ly", type=int, default=LY, help="lattice height (profiling of smaller cases)")
@@ -388,12 +389,73 @@ def run_batch(a):
     b.close()
 
 
+def run_adjoint(a):
+    """Differentiation workload: dE/d(a_1..a_8, tau) of the total kinetic energy after 500
+    FP64 steps of a 512 x 1024 RT lattice (seed 5), checkpoints every 22 steps, against the
+    plain forward run of the same 500 steps."""
+    import torch
+
+    from paper_1703_04594_gb300 import adjoint as A
+    from paper_1703_04594_gb300 import inputs as I
+    from paper_1703_04594_gb300 import lbm
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    lx, ly, n, every, seed = 512, 1024, 500, 22, 5 + rank
+    p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
+    modes = I.rt_modes(lx, ly, seed)
+
+    def forward_only():
+        fields = [t.contiguous().cuda() for t in I.rt_fields(lx, ly, modes, T_BOTTOM, T_TOP, abs(GY))]
+        f = lbm.empty_state(p)
+        lbm.init(p, *fields, f)
+        res = lbm.run(p, f, lbm.empty_state(p), n)
+        return float(lbm.kinetic_energy(p, res))
+
+    def gradient():
+        amp = modes.a.clone().requires_grad_(True)
+        tau = torch.tensor(TAU, dtype=torch.float64, requires_grad=True)
+        fields = I.rt_fields(lx, ly, I.RTModes(a=amp, phi=modes.phi), T_BOTTOM, T_TOP, abs(GY))
+        e = A.kinetic_energy_after(*[t.cuda() for t in fields], tau, p, n, every)
+        e.backward()
+        return amp.grad, tau.grad
+
+    for _ in range(max(1, a.warmup)):
+        forward_only()
+        gradient()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            forward_only()
+        torch.cuda.synchronize()
+        t_fwd = max_over_ranks((time.perf_counter() - t0) / a.steps, "cuda")
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            gradient()
+        torch.cuda.synchronize()
+        t_grad = max_over_ranks((time.perf_counter() - t0) / a.steps, "cuda")
+    if rank == 0:
+        sites = lx * ly
+        line = {"metric": "D2Q37 MLUPS (gradient: forward + checkpointed adjoint)",
+                "value": whole_job_mlups(sites, n, world, t_grad * 1e3), "unit": "MLUPS", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_grad * 1e3 / n, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"dE/d(a_1..a_8, tau), E = kinetic energy after {n} steps of {lx}x{ly}",
+                           "checkpoint_every": every, "repeats": a.steps},
+                "forward_s": t_fwd, "gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "adjoint":
+        run_adjoint(a)
     else:
         run_ours(a)
 

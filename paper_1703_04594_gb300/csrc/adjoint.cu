@@ -38,29 +38,58 @@ struct EqVjp {
   double Grho, Gux, Guy, Gt;
 };
 
-__device__ __forceinline__ EqVjp eq_vjp(double rho, double usx, double usy, double t, const double (&mu)[Q]) {
+// Computed one opposite pair (v, -v) at a time: with s = xi_v . u_s,
+// P(+-s) = E +- O, dP/ds(+-s) = Pse +- Pso, dP/dU(+-s) = PUe +- PUo, dP/dt(+-s) = Pte +- Pto,
+// and S = mu_v + mu_-v, Dm = mu_v - mu_-v, the pair contributes
+//   Grho: w (S E + Dm O);  Gu: w [xi (Dm Pse + S Pso) + 2 u_s (S PUe + Dm PUo)];
+//   Gt: w (S Pte + Dm Pto)   (the factor rho of Gu, Gt applied at the end).
+// `mu(i)` returns mu_i (read on demand, so the 37 values need not stay in registers).
+template <class Mu>
+__device__ __forceinline__ EqVjp eq_vjp_pairs(double rho, double usx, double usy, double t, Mu&& mu) {
   const double U = fma(usx, usx, usy * usy);
-  double Gr = 0.0, Gx = 0.0, Gy = 0.0, Gt = 0.0;
+  const double Ux = C * usx, Uy = C * usy;  // s = v . (Ux, Uy)
+  double Gr, Gx, Gy, Gt;
+  {  // rest population: s = 0, xi = 0
+    const double c0 = 1.0 - 0.5 * U - 0.5 * t * D + 0.125 * U * U + 0.25 * t * U * (D + 2.0) +
+                      0.125 * t * t * D * (D + 2.0);
+    const double pue = -0.5 + 0.25 * U + 0.25 * t * (D + 2.0);
+    const double pt0 = -0.5 * D + 0.25 * U * (D + 2.0) + 0.25 * t * D * (D + 2.0);
+    const double m = mu(0) * weight(0);
+    Gr = m * c0;
+    Gx = m * (2.0 * pue * usx);
+    Gy = m * (2.0 * pue * usy);
+    Gt = m * pt0;
+  }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const double q = C2 * (double)v2(i);
-    const double xix = C * (double)vx(i), xiy = C * (double)vy(i);
-    const double s = fma(xix, usx, xiy * usy);
+  for (int k = 1; k <= NPAIR; ++k) {
+    const double q = C2 * (double)v2(k);
+    const double xix = C * (double)rep_vx(k), xiy = C * (double)rep_vy(k);
     const double c2 = 0.5 - 0.25 * U + 0.25 * t * (q - D - 4.0);
     const double c1 = 1.0 - 0.5 * U + 0.5 * t * (q - D - 2.0);
     const double c0 = 1.0 - 0.5 * U + 0.5 * t * (q - D) + 0.125 * U * U + 0.25 * t * U * (D + 2.0 - q) +
                       0.125 * t * t * (q * q - 2.0 * (D + 2.0) * q + D * (D + 2.0));
-    const double P = fma(s, fma(s, fma(s, fma(s, 1.0 / 24.0, 1.0 / 6.0), c2), c1), c0);
-    const double Ps = fma(s, fma(s, fma(s, 1.0 / 6.0, 0.5), 2.0 * c2), c1);
-    const double PU = (-0.5 + 0.25 * U + 0.25 * t * (D + 2.0 - q)) - 0.5 * s - 0.25 * s * s;
-    const double Pt = (0.5 * (q - D) + 0.25 * U * (D + 2.0 - q) +
-                       0.25 * t * (q * q - 2.0 * (D + 2.0) * q + D * (D + 2.0))) +
-                      0.5 * (q - D - 2.0) * s + 0.25 * (q - D - 4.0) * s * s;
-    const double m = mu[i] * weight(i);
-    Gr = fma(m, P, Gr);
-    Gx = fma(m, fma(Ps, xix, 2.0 * PU * usx), Gx);
-    Gy = fma(m, fma(Ps, xiy, 2.0 * PU * usy), Gy);
-    Gt = fma(m, Pt, Gt);
+    const double pue0 = -0.5 + 0.25 * U + 0.25 * t * (D + 2.0 - q);
+    const double pt0 = 0.5 * (q - D) + 0.25 * U * (D + 2.0 - q) +
+                       0.25 * t * (q * q - 2.0 * (D + 2.0) * q + D * (D + 2.0));
+    const double s = fma((double)rep_vx(k), Ux, (double)rep_vy(k) * Uy);
+    const double s2 = s * s;
+    const double E = fma(s2, fma(s2, 1.0 / 24.0, c2), c0);
+    const double O = s * fma(s2, 1.0 / 6.0, c1);
+    const double Pse = fma(0.5, s2, c1);
+    const double Pso = s * fma(s2, 1.0 / 6.0, 2.0 * c2);
+    const double PUe = fma(-0.25, s2, pue0);
+    const double PUo = -0.5 * s;
+    const double Pte = fma(0.25 * (q - D - 4.0), s2, pt0);
+    const double Pto = 0.5 * (q - D - 2.0) * s;
+    const double w = weight(k);
+    const double mp = mu(k), mm = mu(k + NPAIR);
+    const double S = (mp + mm) * w, Dm = (mp - mm) * w;
+    Gr = fma(S, E, fma(Dm, O, Gr));
+    const double xiPart = fma(Dm, Pse, S * Pso);
+    const double uPart = 2.0 * fma(S, PUe, Dm * PUo);
+    Gx = fma(xix, xiPart, fma(uPart, usx, Gx));
+    Gy = fma(xiy, xiPart, fma(uPart, usy, Gy));
+    Gt = fma(S, Pte, fma(Dm, Pto, Gt));
   }
   return {Gr, rho * Gx, rho * Gy, rho * Gt};
 }
@@ -79,7 +108,7 @@ __device__ __forceinline__ double block_sum_128(double v) {
 
 // Step 1: per-site adjoint of the collision (block 32 x 4 as the forward kernels).
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128) k_adj_collide(const double* __restrict__ fin,
+__global__ void __launch_bounds__(128, 3) k_adj_collide(const double* __restrict__ fin,
                                                      const double* __restrict__ lam_next, double* __restrict__ out,
                                                      double* __restrict__ dtau_part, StepArgs a, double tau, double gx,
                                                      double gy) {
@@ -104,22 +133,23 @@ __global__ void __launch_bounds__(128) k_adj_collide(const double* __restrict__ 
       const double usx = fma(tau, gx, ux), usy = fma(tau, gy, uy);
       const double t = T + tau * (1.0 - tau) * gg / D - 1.0;
       const long long o = (long long)x * a.pitch + y;
-      double mu[Q];
+      const double* lam = lam_next + o;
+      double mu_ft = 0.0;  // sum_i mu_i f~_i
 #pragma unroll
-      for (int i = 0; i < Q; ++i) mu[i] = __ldg(lam_next + o + i * a.pop);
-      const EqVjp G = eq_vjp(rho, usx, usy, t, mu);
+      for (int i = 0; i < Q; ++i) mu_ft = fma(__ldg(lam + i * a.pop), f[i], mu_ft);
+      const EqVjp G = eq_vjp_pairs(rho, usx, usy, t, [&](int i) { return __ldg(lam + i * a.pop); });
       const double nuE = G.Gt * inv / D;
       const double nuJx = G.Gux * inv - 2.0 * ux * G.Gt * inv / D;
       const double nuJy = G.Guy * inv - 2.0 * uy * G.Gt * inv / D;
       const double nuR = G.Grho - (G.Gux * ux + G.Guy * uy) * inv + G.Gt * (-E * inv + 2.0 * uu) * inv / D;
       const double om = 1.0 / tau, om1 = 1.0 - om;
-      double mu_ft = 0.0;
+      __stcs(out + o, fma(om1, __ldg(lam), om * nuR));
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const double xix = C * (double)vx(i), xiy = C * (double)vy(i), q = C2 * (double)v2(i);
-        const double v = fma(om1, mu[i], om * (nuR + nuJx * xix + nuJy * xiy + nuE * q));
-        __stcs(out + o + i * a.pop, v);
-        mu_ft = fma(mu[i], f[i], mu_ft);
+      for (int k = 1; k <= NPAIR; ++k) {  // out_{+-v} = (1-w) mu + w (nuR + nuE q +- nuJ . xi)
+        const double A = fma(nuE, C2 * (double)v2(k), nuR);
+        const double B = fma(nuJx, C * (double)rep_vx(k), nuJy * (C * (double)rep_vy(k)));
+        __stcs(out + o + k * a.pop, fma(om1, __ldg(lam + k * a.pop), om * (A + B)));
+        __stcs(out + o + (k + NPAIR) * a.pop, fma(om1, __ldg(lam + (k + NPAIR) * a.pop), om * (A - B)));
       }
       // sum_i mu_i f^eq_i = rho * Grho
       contrib = -(rho * G.Grho - mu_ft) * om * om + om * (G.Gux * gx + G.Guy * gy + G.Gt * (1.0 - 2.0 * tau) * gg / D);
@@ -216,10 +246,7 @@ __global__ void __launch_bounds__(128) k_init_adjoint(const double* __restrict__
   if (x >= a.lx || y >= a.ly) return;
   const long long fi = (long long)x * a.ly + y;
   const long long o = (long long)x * a.pitch + y;
-  double mu[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) mu[i] = __ldg(lam + o + i * a.pop);
-  const EqVjp G = eq_vjp(rho[fi], ux[fi], uy[fi], T[fi] - 1.0, mu);
+  const EqVjp G = eq_vjp_pairs(rho[fi], ux[fi], uy[fi], T[fi] - 1.0, [&](int i) { return __ldg(lam + o + i * a.pop); });
   g_rho[fi] = G.Grho;
   g_ux[fi] = G.Gux;
   g_uy[fi] = G.Guy;

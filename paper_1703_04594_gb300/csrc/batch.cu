@@ -117,7 +117,7 @@ __device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, l
 // Register cap: at most 256 threads per block (8 warps); the FP32 step keeps two such
 // blocks resident per SM (<= 128 registers), as the single-lattice FP32 kernel does.
 template <class T, bool PERIODIC>
-__global__ void __launch_bounds__(256) k_batch_step(const BatchLattice* __restrict__ L,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_batch_step(const BatchLattice* __restrict__ L,
                                                     const unsigned short* __restrict__ tl, long long total,
                                                     int parity) {
   const long long t = blockIdx.x;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_batch_step(const BatchLattice* __restri
 }
 
 template <class T, bool PERIODIC>
-__global__ void __launch_bounds__(256) k_batch_persistent(const BatchLattice* __restrict__ L,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_batch_persistent(const BatchLattice* __restrict__ L,
                                                           const unsigned short* __restrict__ tl, long long total,
                                                           int parity0, int steps, BatchSync* sync, unsigned phantom,
                                                           long long timeout_ns) {

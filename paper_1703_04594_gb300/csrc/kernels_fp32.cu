@@ -9,7 +9,7 @@
 namespace d2q37 {
 
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ fin, float* __restrict__ fout,
+__global__ void __launch_bounds__(128, 6) k_step_fp32(const float* __restrict__ fin, float* __restrict__ fout,
                                                    StepArgs a) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp

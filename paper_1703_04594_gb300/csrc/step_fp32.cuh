@@ -1,10 +1,11 @@
 // FP32 shifted-deviation storage: the state holds g_i = f_i - w_i rho0 as float.
 //
 // Precision split (same step as the FP64 path: propagate -> bc -> collide, Sec. 5):
-//  * moments (eq. "macro") are accumulated in 64-bit fixed point with 2^-52 resolution:
-//    every stored float of magnitude >= 2^-29 converts exactly, the integer sums are
-//    exact and order-independent (error <= 37 * 2^-52 from the tiny values, the same
-//    order as a float64 accumulation), and the sums are then converted to float64;
+//  * moments (eq. "macro") are accumulated in fixed point with 2^-52 resolution: every
+//    stored float of magnitude >= 2^-29 splits exactly into three int32 parts (split3),
+//    the integer sums are exact and order-independent (error <= 37 * 2^-53 from the tiny
+//    values, the same order as a float64 accumulation), and the sums are then converted
+//    to float64;
 //  * density, energy and the temperature t = T_s - 1 (the equilibrium's temperature
 //    terms) are formed in float64 from those sums; 1/rho is a float32 seed refined by one
 //    float64 Newton step;
@@ -23,57 +24,74 @@ constexpr int FIX = 52;                                   // fixed-point fractio
 constexpr double FIX_SCALE = 1.0 / 4503599627370496.0;    // 2^-52
 constexpr float FIX_SCALE_F = 1.0f / 4503599627370496.0f;
 
-// 32-bit shifts with PTX semantics: shift counts >= 32 give 0.
-__device__ __forceinline__ unsigned shl_clamp(unsigned x, unsigned s) {
-  unsigned r;
-  asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
-  return r;
-}
-__device__ __forceinline__ unsigned shr_clamp(unsigned x, unsigned s) {
-  unsigned r;
-  asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
-  return r;
-}
+// Exact split of a float |v| < 16 into three integers with v * 2^52 = H * 2^34 + R * 2^11 + L
+// (|H|, |R| <= 2^22, |L| <= 2^10), done with float additions of power-of-two constants so
+// that it runs on the FMA pipe instead of the integer pipe:
+//   h1 = fl(v + 48) lies in [32, 64), where floats are spaced 2^-18 apart, so it rounds v to
+//   a multiple of 2^-18, and within that binade the bit pattern grows by one per 2^-18:
+//   H = bits(h1) - bits(48).  r1 = v - (h1 - 48) is exact (|r1| <= 2^-19).  The same with
+//   1.5 * 2^-18 (binade [2^-18, 2^-17), spacing 2^-41) gives R and an exact rest r2,
+//   |r2| <= 2^-42, and one FMA with 1.5 * 2^23 rounds r2 * 2^52 to the integer L.
+// Floats of magnitude >= 2^-29 convert exactly; smaller ones are rounded at 2^-52.
+struct Fix3 {
+  int H, R, L;
+};
 
-// Float -> 64-bit fixed point (value * 2^52), exact for 2^-29 <= |v| < 16; smaller
-// magnitudes are truncated below 2^-52; zero and subnormals give 0.
-__device__ __forceinline__ long long to_fix(float v) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned m = (b & 0x7fffffu) | 0x800000u;
-  const int sh = (int)((b >> 23) & 0xffu) - (150 - FIX);  // v = m * 2^(e - 150)
-  unsigned lo, hi;
-  if (sh >= 0) {
-    lo = shl_clamp(m, (unsigned)sh);
-    hi = __funnelshift_lc(m, 0u, (unsigned)sh);
-  } else {
-    lo = shr_clamp(m, (unsigned)(-sh));
-    hi = 0u;
-  }
-  const long long x = (long long)(((unsigned long long)hi << 32) | lo);
-  const long long s = (long long)((int)b >> 31);  // 0 or -1
-  return (x ^ s) - s;
+__device__ __forceinline__ Fix3 split3(float v) {
+  constexpr float C1 = 48.0f;                   // 1.5 * 2^5
+  constexpr float C2 = 5.7220458984375e-06f;    // 1.5 * 2^-18
+  constexpr float C3 = 12582912.0f;             // 1.5 * 2^23
+  constexpr float S52 = 4503599627370496.0f;    // 2^52
+  const float h1 = __fadd_rn(v, C1);
+  const float r1 = __fsub_rn(v, __fsub_rn(h1, C1));
+  const float h2 = __fadd_rn(r1, C2);
+  const float r2 = __fsub_rn(r1, __fsub_rn(h2, C2));
+  const float h3 = __fmaf_rn(r2, S52, C3);
+  return {__float_as_int(h1) - __float_as_int(C1), __float_as_int(h2) - __float_as_int(C2),
+          __float_as_int(h3) - __float_as_int(C3)};
 }
 
 struct FixMoments {
   long long drho, jx, jy, de;  // sum g, sum vx g, sum vy g, sum |v|^2 g  (all * 2^52)
 };
 
+__device__ __forceinline__ long long join3(int H, int R, int L) {
+  return ((long long)H << 34) + ((long long)R << 11) + (long long)L;
+}
+
+// Streaming: each opposite pair is split and added to the four sums at once, in three
+// int32 lanes per sum (no overflow for |g| < 16: |sum| < 108 * 2^23 per lane).
 __device__ __forceinline__ FixMoments moments_fix(const float (&g)[Q]) {
-  // streaming: each opposite pair is converted and added to the four sums at once
-  FixMoments r;
-  r.drho = to_fix(g[0]);
-  r.de = 0;
-  r.jx = 0;
-  r.jy = 0;
+  const Fix3 z = split3(g[0]);
+  int rH = z.H, rR = z.R, rL = z.L;
+  int eH = 0, eR = 0, eL = 0, xH = 0, xR = 0, xL = 0, yH = 0, yR = 0, yL = 0;
 #pragma unroll
   for (int k = 1; k <= NPAIR; ++k) {
-    const long long a = to_fix(g[k]), b = to_fix(g[k + NPAIR]);
-    const long long P = a + b, M = a - b;
-    r.drho += P;
-    r.de += (long long)v2(k) * P;
-    if (rep_vx(k) != 0) r.jx += (long long)rep_vx(k) * M;
-    if (rep_vy(k) != 0) r.jy += (long long)rep_vy(k) * M;
+    const Fix3 a = split3(g[k]), b = split3(g[k + NPAIR]);
+    const int PH = a.H + b.H, PR = a.R + b.R, PL = a.L + b.L;
+    const int MH = a.H - b.H, MR = a.R - b.R, ML = a.L - b.L;
+    rH += PH;
+    rR += PR;
+    rL += PL;
+    eH += v2(k) * PH;
+    eR += v2(k) * PR;
+    eL += v2(k) * PL;
+    if (rep_vx(k) != 0) {
+      xH += rep_vx(k) * MH;
+      xR += rep_vx(k) * MR;
+      xL += rep_vx(k) * ML;
+    }
+    if (rep_vy(k) != 0) {
+      yH += rep_vy(k) * MH;
+      yR += rep_vy(k) * MR;
+      yL += rep_vy(k) * ML;
+    }
   }
+  FixMoments r;
+  r.drho = join3(rH, rR, rL);
+  r.de = join3(eH, eR, eL);
+  r.jx = join3(xH, xR, xL);
+  r.jy = join3(yH, yR, yL);
   return r;
 }
 

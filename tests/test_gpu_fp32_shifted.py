@@ -99,3 +99,22 @@ def test_kinetic_energy_fp32_close_to_fp64():
     r32 = lbm.run(p32, device_init(p32, fields), lbm.empty_state(p32), 50)
     k64, k32 = float(lbm.kinetic_energy(p64, r64)), float(lbm.kinetic_energy(p32, r32))
     assert abs(k32 - k64) <= 1e-4 * k64
+
+
+def test_moment_sums_are_exact_sums_of_the_stored_floats():
+    """The FP32 path accumulates the stored deviations in fixed point: the density must be
+    rho0 + (the exactly rounded sum of the 37 stored floats), checked with math.fsum on
+    every site of a small lattice."""
+    import math
+    p = fp32(lbm.Params(24, 40, gx=2e-4))
+    fields = rt_fields(p, seed=6)
+    fields = (fields[0], fields[1] + 0.01, fields[2] - 0.02, fields[3])
+    f = lbm.run(p, device_init(p, fields), lbm.empty_state(p), 3)
+    rho = lbm.moments(p, f)[0].cpu()
+    g = f[:, :, : p.ly].double().cpu()
+    worst = 0.0
+    for x in range(p.lx):
+        for y in range(p.ly):
+            exact = p.rho0 + math.fsum(g[:, x, y].tolist())
+            worst = max(worst, abs(float(rho[x, y]) - exact) / exact)
+    assert worst <= 2.3e-16, worst

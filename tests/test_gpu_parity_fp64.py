@@ -183,3 +183,19 @@ def test_full_size_sampled_columns():
         assert rel_err(got[:, x].double().cpu(), want) <= STEP_TOL, x
     del fa, fb, res, got
     torch.cuda.empty_cache()
+
+
+def test_fixed_point_moment_sums_within_float64_summation_error():
+    """The FP64 path sums the populations in 64-bit fixed point (2^-52 resolution, rounded):
+    the density differs from the exactly rounded sum by at most 37 * 2^-53 + 1 ulp."""
+    import math
+    p = lbm.Params(24, 40, gx=2e-4)
+    f = lbm.run(p, device_init(p, rt_fields(p, seed=6)), lbm.empty_state(p), 3)
+    rho = lbm.moments(p, f)[0].cpu()
+    g = f[:, :, : p.ly].cpu()
+    worst = 0.0
+    for x in range(p.lx):
+        for y in range(p.ly):
+            exact = math.fsum(g[:, x, y].tolist())
+            worst = max(worst, abs(float(rho[x, y]) - exact))
+    assert worst <= 37 * 2.0 ** -53 + 2.3e-16, worst
