@@ -8,7 +8,7 @@ shape).  One bench step = one fused propagate + bc + collide pass over the whole
 lattice (one kernel launch).  Each state buffer is 9.9 GB, far larger than the 129 MB
 L2, so no L2 flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--variant fused|separate]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--variant fused|separate|push|aos|psoa|caosoa]
     python bench.py --impl reference      # the float64 CPU oracle on a bounded sample
 
 Under torchrun (N > 1) every rank steps its own replica lattice (independent problems:
@@ -62,9 +62,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant", choices=["fused", "separate", "aos", "csoa"], default="fused",
-                    help="fused SoA step; separate propagate/bc/collide kernels; fused step in AoS or "
-                         "clustered-SoA layout (FP64)")
+    ap.add_argument("--variant", choices=["fused", "separate", "push", "aos", "psoa", "caosoa"], default="fused",
+                    help="fused SoA step; separate propagate/bc/collide kernels with the pull or push "
+                         "propagate; fused step in the AoS, partitioned-SoA or CAoSoA layout (FP64)")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32 = FP32 shifted-deviation storage (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -216,10 +216,12 @@ def run_ours(a):
     fields = I.rt_state(lx, ly, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))
     dev = [t.contiguous().cuda() for t in fields]
     fa, fb = lbm.empty_state(p), lbm.empty_state(p)
-    ftmp = lbm.empty_state(p) if a.variant == "separate" else None
+    separate = a.variant in ("separate", "push")
+    ftmp = lbm.empty_state(p) if separate else None
     lbm.init(p, *dev, fa)
     stream = torch.cuda.current_stream()
-    layout = {"aos": lbm.LAYOUT_AOS, "csoa": lbm.LAYOUT_CSOA}.get(a.variant)
+    layout = {"aos": lbm.LAYOUT_AOS, "psoa": lbm.LAYOUT_PSOA, "caosoa": lbm.LAYOUT_CAOSOA}.get(a.variant)
+    prop = lbm.propagate_push if a.variant == "push" else lbm.propagate
     if layout is not None:
         if fp32:
             raise SystemExit("layout variants run the FP64 step")
@@ -232,7 +234,7 @@ def run_ours(a):
         elif layout is not None:
             lbm.step_layout(p, layout, src, dst, stream)
         else:
-            lbm.propagate(p, src, ftmp, stream)
+            prop(p, src, ftmp, stream)
             lbm.bc(p, src, ftmp, stream)
             lbm.collide(p, ftmp, dst, stream)
 
@@ -271,9 +273,29 @@ def run_ours(a):
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(a.variant),
                     "kernel": {"fused": "k_step_fp64", "separate": "whole step (3 kernels)",
-                               "aos": "k_step_layout<AoS>", "csoa": "k_step_layout<CSoA>"}[a.variant],
+                               "push": "whole step (3 kernels)", "aos": "k_step_layout<AoS>",
+                               "psoa": "k_step_layout<PSoA>", "caosoa": "k_step_layout<CAoSoA>"}[a.variant],
                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                     "hbm_gbs_equiv": BYTES_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e9}
+
+    # the propagate kernel alone (Table "propagate-kernel" of Sec. 4): a pure copy of every
+    # population whose source is inside the fluid, timed over the same number of launches
+    prop_line = None
+    if separate:
+        wall_entries = 0 if p.bc == lbm.BC_PERIODIC_Y else lx * sum(abs(v) for v in lbm.model()[3])
+        prop_bytes = 2 * 8 * (37 * sites - wall_entries)
+        pev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        prop(p, bufs[0], ftmp, stream)
+        pev[0].record(stream)
+        for k in range(a.steps):
+            prop(p, bufs[k % 2], ftmp, stream)
+        pev[1].record(stream)
+        torch.cuda.synchronize()
+        prop_ms = pev[0].elapsed_time(pev[1]) / a.steps
+        gbs = prop_bytes / (prop_ms * 1e-3) / 1e9
+        prop_line = {"kernel": "k_propagate_push_fp64" if a.variant == "push" else "k_propagate_fp64",
+                     "ms": prop_ms, "bytes": prop_bytes, "achieved": gbs, "unit": "GB/s",
+                     "frac": gbs / HBM_PEAK_GBS, "peak": HBM_PEAK_GBS}
 
     # end to end through the C-ABI from pinned host fields: H2D, init, K steps, moments, D2H
     pinned_in = [t.contiguous().pin_memory() for t in fields]
@@ -303,7 +325,8 @@ def run_ours(a):
                            "l2": "state buffers >= 4.9 GB >> 129 MB L2; no flush needed",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e,
-                "gpu_launches": a.steps * (3 if a.variant == "separate" else 1),
+                **({"propagate_kernel": prop_line} if prop_line else {}),
+                "gpu_launches": a.steps * (3 if separate else 1),
                 "clocks": clk.summary()}
         if not a.no_cpu_baseline and world == 1 and (lx, ly) == (LX, LY):
             line["cpu_baseline"] = oracle_sample(4)

@@ -99,6 +99,12 @@ int32_t lbm_run(const lbm_params* p, void* f_a_dev, void* f_b_dev, int32_t n_ste
  * propagate -> bc -> collide equals lbm_step up to floating-point contraction order.
  * FP64 only. */
 int32_t lbm_propagate(const lbm_params* p, const void* f_in_dev, void* f_tmp_dev, void* stream);
+/* The push form of the same propagate (Sec. 4, "push" vs "pull"): every site moves its own
+ * 37 populations to (x + vx_i mod lx, y + vy_i), dropping moves that leave the fluid.  Reads
+ * are aligned and writes are shifted, the opposite of the pull form.  It writes exactly the
+ * entries lbm_propagate writes, with the same values (a copy, so bit-identical), and
+ * leaves the same entries for lbm_bc.  Same arguments, layout and errors as lbm_propagate. */
+int32_t lbm_propagate_push(const lbm_params* p, const void* f_in_dev, void* f_tmp_dev, void* stream);
 int32_t lbm_bc(const lbm_params* p, const void* f_in_dev, void* f_tmp_dev, void* stream);
 int32_t lbm_collide(const lbm_params* p, const void* f_tmp_dev, void* f_out_dev, void* stream);
 
@@ -144,17 +150,28 @@ int32_t lbm_simulate_host(const lbm_params* p, const double* rho_host, const dou
                           double* T_out_host, void* f_a_dev, void* f_b_dev, double* fields_dev,
                           void* stream);
 
-/* ---- Layout comparison (Sec. 4: AoS vs SoA vs clustered SoA), FP64 fused step, walls ----
- * LBM_LAYOUT_SOA is the layout of every other entry point.  LBM_LAYOUT_AOS stores the 37
- * populations of a site contiguously: element (i, x, y) at (x * pitch + y) * 37 + i.
- * LBM_LAYOUT_CSOA splits each population column into 32 partitions of P = pitch / 32 rows
- * and packs the k-th rows of the partitions into 32-wide clusters: element (i, x, y) at
- * ((i * lx + x) * P + j) * 32 + k with y = k * P + j.  Same buffer size in every layout. */
-enum lbm_layout { LBM_LAYOUT_SOA = 0, LBM_LAYOUT_AOS = 1, LBM_LAYOUT_CSOA = 2 };
-/* dst = src re-laid out (SoA <-> AoS, SoA <-> CSoA); dst and src must not be the same. */
+/* ---- Layout comparison (Sec. 4: AoS, SoA, CSoA, CAoSoA), FP64 fused step, walls ----
+ * LBM_LAYOUT_SOA is the layout of every other entry point: element (i, x, y) at
+ * (i * lx + x) * pitch + y.  With pitch a multiple of 32 it is also the paper's CSoA
+ * ("Cluster Structure of Array") with cluster width VL = 32 = the warp: every run of 32
+ * consecutive y of one population is one aligned 256-byte cluster.
+ * LBM_LAYOUT_AOS stores the 37 populations of a site contiguously: element (i, x, y) at
+ * (x * pitch + y) * 37 + i.
+ * The two partitioned layouts split each column into 32 partitions of P = pitch / 32 rows;
+ * row y = k * P + j is element k of cluster j (the paper's CAoSoA partitioning):
+ *   LBM_LAYOUT_PSOA   keeps one array per population: element (i, x, y) at
+ *                     ((i * lx + x) * P + j) * 32 + k;
+ *   LBM_LAYOUT_CAOSOA ("Clustered Array of Structure of Array") keeps the 37 clusters of
+ *                     one (x, j) adjacent: element (i, x, y) at ((x * P + j) * 37 + i) * 32 + k.
+ * Same buffer size (lbm_buffer_bytes) in every layout. */
+enum lbm_layout { LBM_LAYOUT_SOA = 0, LBM_LAYOUT_AOS = 1, LBM_LAYOUT_PSOA = 2, LBM_LAYOUT_CAOSOA = 3 };
+/* dst = src re-laid out between SoA and one of AOS, PSOA, CAOSOA (either direction); dst
+ * and src must not be the same.  Exact copy. */
 int32_t lbm_convert_layout(const lbm_params* p, int32_t from, const void* src_dev, int32_t to, void* dst_dev,
                            void* stream);
-/* One fused step of a state stored in layout AOS or CSOA (results bit-identical to lbm_step). */
+/* One fused step of a state stored in layout AOS, PSOA or CAOSOA (the same arithmetic as
+ * lbm_step on the same gathered values; results agree with lbm_step up to the compiler's
+ * contraction of multiply-adds). */
 int32_t lbm_step_layout(const lbm_params* p, int32_t layout, const void* f_in_dev, void* f_out_dev, void* stream);
 
 /* ---- Adjoint (reverse mode) of the FP64 step, for gradients of observables ----

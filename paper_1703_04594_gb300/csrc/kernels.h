@@ -34,6 +34,7 @@ struct StepArgs : StepScalars, StepWalls {};
 
 cudaError_t launch_step_fp64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_propagate_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_propagate_push_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_bc_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_collide_fp64(const double* ftmp, double* fout, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy, const double* T, double* f,

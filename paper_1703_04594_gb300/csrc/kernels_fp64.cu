@@ -57,6 +57,29 @@ __global__ void __launch_bounds__(128) k_propagate_fp64(const double* __restrict
   }
 }
 
+// Push form of propagate: site (x, y) sends each of its populations to (x + vx, y + vy).
+// A warp reads 32 consecutive y of one population (one aligned 256-byte run) and writes
+// them shifted by the hop, so the writes are the unaligned side.  Moves that leave the fluid
+// in y are dropped; the entries they would have fed from outside are left for bc.
+template <bool PERIODIC>
+__global__ void __launch_bounds__(128) k_propagate_push_fp64(const double* __restrict__ fin,
+                                                             double* __restrict__ ftmp, StepArgs a) {
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  const int y = blockIdx.x * 32 + threadIdx.x;
+  if (x >= a.lx || y >= a.ly) return;
+  long long col[7];  // destination column offsets for vx = -3..3
+#pragma unroll
+  for (int d = 0; d < 7; ++d) col[d] = (long long)wrap(x + (d - 3), a.lx) * a.pitch;
+  const double* src = fin + (long long)x * a.pitch + y;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int yd = y + vy(i);
+    if (PERIODIC) yd = wrap(yd, a.ly);
+    else if (yd < 0 || yd >= a.ly) continue;  // leaves the fluid
+    __stcs(ftmp + i * a.pop + col[vx(i) + 3] + yd, __ldg(src + i * a.pop));
+  }
+}
+
 // One thread per (column x, wall row r in 0..5): rows 0,1,2 and ly-3, ly-2, ly-1.
 __global__ void __launch_bounds__(128) k_bc_fp64(const double* __restrict__ fin, double* __restrict__ ftmp,
                                                  StepArgs a) {
@@ -186,6 +209,12 @@ cudaError_t launch_step_fp64(const double* fin, double* fout, const StepArgs& a,
 cudaError_t launch_propagate_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s) {
   if (a.periodic) k_propagate_fp64<true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, ftmp, a);
   else k_propagate_fp64<false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, ftmp, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_push_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s) {
+  if (a.periodic) k_propagate_push_fp64<true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, ftmp, a);
+  else k_propagate_push_fp64<false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, ftmp, a);
   return cudaGetLastError();
 }
 

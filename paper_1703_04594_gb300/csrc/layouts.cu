@@ -1,18 +1,22 @@
 // Alternative population layouts for the fused FP64 step (the layout comparison of Sec. 4,
-// Table "propagate-kernel"/"collide-kernel": AoS, SoA, clustered SoA).  Same arithmetic as
-// the SoA step (collide_site), so every layout gives bit-identical results; only the
-// addresses of the 37 gathers and stores change.  Walls only (no periodic-y mode).
+// Tables "propagate-kernel"/"collide-kernel": AoS, SoA, CSoA, CAoSoA).  Same arithmetic as
+// the SoA step (collide_site) on the same gathered values; only the addresses of the 37
+// gathers and stores change.  Walls only (no periodic-y mode).
 //
-//   AoS:  element (i, x, y) at (x * pitch + y) * 37 + i: the 37 populations of a site are
-//         contiguous (Sec. 4 "AoS").  A warp still owns 32 consecutive y of one column, so
-//         each of its loads touches 32 records 296 bytes apart.
-//   CSoA: element (i, x, y) at ((i * lx + x) * P + j) * 32 + k with y = k * P + j and
-//         P = pitch / 32: every population column is split into 32 partitions of P rows and
-//         the k-th elements of the partitions form a 32-wide cluster (the paper's clustering
-//         of Sec. 4, with the cluster width set to the warp).  A warp owns cluster (x, j):
-//         lane k is site y = k * P + j, so a hop by vy reads cluster j - vy of the same lanes,
-//         one aligned 256-byte run, except across a partition edge, where lane k reads
-//         lane k -/+ 1 of cluster j - vy +/- P.
+//   SoA:    the production layout.  With pitch a multiple of 32 it is the paper's CSoA with
+//           cluster width 32: a warp's 32 consecutive y are one aligned 256-byte cluster.
+//   AoS:    element (i, x, y) at (x * pitch + y) * 37 + i: the 37 populations of a site are
+//           contiguous (Sec. 4 "AoS").  A warp still owns 32 consecutive y of one column, so
+//           each of its loads touches 32 records 296 bytes apart.
+//   PSoA:   element (i, x, y) at ((i * lx + x) * P + j) * 32 + k with y = k * P + j and
+//           P = pitch / 32: every population column is split into 32 partitions of P rows
+//           and the k-th elements of the partitions form a 32-wide cluster (the partitioning
+//           of the paper's CAoSoA, one array per population).
+//   CAoSoA: the same clusters, with the 37 clusters of one (x, j) adjacent (Sec. 4
+//           "CAoSoA"): element (i, x, y) at ((x * P + j) * 37 + i) * 32 + k.
+// In both partitioned layouts a warp owns cluster (x, j): lane k is site y = k * P + j, so a
+// hop by vy reads cluster j - vy of the same lanes, one aligned 256-byte run, except across
+// a partition edge, where lane k reads lane k -/+ 1 of cluster j - vy +/- P.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,16 +32,24 @@ __device__ __forceinline__ long long aos_index(const StepArgs& a, int i, int x, 
   return ((long long)x * a.pitch + y) * Q + i;
 }
 
-__device__ __forceinline__ long long csoa_index(const StepArgs& a, int i, int x, int y) {
+// Element k of cluster j of population i in column x, partitioned layouts.
+template <int L>
+__device__ __forceinline__ long long cluster_index(const StepArgs& a, int i, int x, long long j, long long k) {
   const long long P = a.pitch >> 5;
-  const long long k = y / P, j = y - k * P;
+  if (L == LBM_LAYOUT_CAOSOA) return (((long long)x * P + j) * Q + i) * 32 + k;
   return (((long long)i * a.lx + x) * P + j) * 32 + k;
 }
+
+constexpr bool partitioned(int L) { return L == LBM_LAYOUT_PSOA || L == LBM_LAYOUT_CAOSOA; }
 
 template <int L>
 __device__ __forceinline__ long long lindex(const StepArgs& a, int i, int x, int y) {
   if (L == LBM_LAYOUT_AOS) return aos_index(a, i, x, y);
-  if (L == LBM_LAYOUT_CSOA) return csoa_index(a, i, x, y);
+  if (partitioned(L)) {
+    const long long P = a.pitch >> 5;
+    const long long k = y / P;
+    return cluster_index<L>(a, i, x, y - k * P, k);
+  }
   return (long long)i * a.pop + (long long)x * a.pitch + y;
 }
 
@@ -50,8 +62,8 @@ __device__ __forceinline__ double column_density(const double* __restrict__ f, c
   return r;
 }
 
-// Fused step of site (x, y) in layout L (walls).  All lanes of a warp share x; for CSoA the
-// warp is cluster j (uniform) and lane k is row y = k * P + j.
+// Fused step of site (x, y) in layout L (walls).  All lanes of a warp share x; in the
+// partitioned layouts the warp is cluster j (uniform) and lane k is row y = k * P + j.
 template <int L>
 __device__ __forceinline__ void step_site_layout(const double* __restrict__ fin, double* __restrict__ fout,
                                                  const StepArgs& a, int x, int y, int j, bool active) {
@@ -75,7 +87,7 @@ __device__ __forceinline__ void step_site_layout(const double* __restrict__ fin,
     const int xs = wrap_index(x - vx(i), a.lx);
     long long idx;
     int ys;
-    if (L == LBM_LAYOUT_CSOA) {
+    if (partitioned(L)) {
       int js = j - vy(i), ks = lane;  // partition arithmetic: uniform branches on js
       if (P >= 3) {                   // a hop crosses at most one partition edge
         if (js < 0) {
@@ -96,7 +108,7 @@ __device__ __forceinline__ void step_site_layout(const double* __restrict__ fin,
         }
       }
       ys = ks * (int)P + js;
-      idx = (((long long)i * a.lx + xs) * P + js) * 32 + ks;
+      idx = cluster_index<L>(a, i, xs, js, ks);
     } else {
       ys = y - vy(i);
       idx = aos_index(a, i, xs, ys);
@@ -117,7 +129,7 @@ __global__ void __launch_bounds__(128) k_step_layout(const double* __restrict__ 
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp
   int y, j = 0;
-  if (L == LBM_LAYOUT_CSOA) {
+  if (partitioned(L)) {
     j = blockIdx.x;  // cluster j, lane k = threadIdx.x
     y = (int)threadIdx.x * (int)(a.pitch >> 5) + j;
   } else {
@@ -138,7 +150,7 @@ __global__ void __launch_bounds__(128) k_convert(const double* __restrict__ src,
 
 template <int L>
 cudaError_t launch_step_layout(const double* fin, double* fout, const StepArgs& a, cudaStream_t s) {
-  const dim3 grid(L == LBM_LAYOUT_CSOA ? (unsigned)(a.pitch >> 5) : (unsigned)((a.ly + 31) / 32),
+  const dim3 grid(partitioned(L) ? (unsigned)(a.pitch >> 5) : (unsigned)((a.ly + 31) / 32),
                   (unsigned)((a.lx + 3) / 4));
   k_step_layout<L><<<grid, dim3(32, 4), 0, s>>>(fin, fout, a);
   return cudaGetLastError();
@@ -149,9 +161,11 @@ cudaError_t launch_convert(int from, int to, const double* src, double* dst, con
 #define LBM_CONV(F, T) \
   if (from == F && to == T) k_convert<F, T><<<grid, blk, 0, s>>>(src, dst, a);
   LBM_CONV(LBM_LAYOUT_SOA, LBM_LAYOUT_AOS)
-  LBM_CONV(LBM_LAYOUT_SOA, LBM_LAYOUT_CSOA)
+  LBM_CONV(LBM_LAYOUT_SOA, LBM_LAYOUT_PSOA)
+  LBM_CONV(LBM_LAYOUT_SOA, LBM_LAYOUT_CAOSOA)
   LBM_CONV(LBM_LAYOUT_AOS, LBM_LAYOUT_SOA)
-  LBM_CONV(LBM_LAYOUT_CSOA, LBM_LAYOUT_SOA)
+  LBM_CONV(LBM_LAYOUT_PSOA, LBM_LAYOUT_SOA)
+  LBM_CONV(LBM_LAYOUT_CAOSOA, LBM_LAYOUT_SOA)
 #undef LBM_CONV
   return cudaGetLastError();
 }
@@ -163,8 +177,10 @@ using namespace d2q37;
 extern "C" {
 
 int32_t lbm_convert_layout(const lbm_params* p, int32_t from, const void* src, int32_t to, void* dst, void* stream) {
-  const bool ok_pair = (from == LBM_LAYOUT_SOA && (to == LBM_LAYOUT_AOS || to == LBM_LAYOUT_CSOA)) ||
-                       (to == LBM_LAYOUT_SOA && (from == LBM_LAYOUT_AOS || from == LBM_LAYOUT_CSOA));
+  const auto other = [](int32_t l) {
+    return l == LBM_LAYOUT_AOS || l == LBM_LAYOUT_PSOA || l == LBM_LAYOUT_CAOSOA;
+  };
+  const bool ok_pair = (from == LBM_LAYOUT_SOA && other(to)) || (to == LBM_LAYOUT_SOA && other(from));
   if (!params_valid(p) || p->precision != LBM_FP64 || !ok_pair || !src || !dst || src == dst ||
       ((uintptr_t)src % 16) || ((uintptr_t)dst % 16))
     return LBM_EINVAL;
@@ -184,7 +200,8 @@ int32_t lbm_step_layout(const lbm_params* p, int32_t layout, const void* fin, vo
   cudaError_t e;
   switch (layout) {
     case LBM_LAYOUT_AOS: e = launch_step_layout<LBM_LAYOUT_AOS>((const double*)fin, (double*)fout, a, (cudaStream_t)stream); break;
-    case LBM_LAYOUT_CSOA: e = launch_step_layout<LBM_LAYOUT_CSOA>((const double*)fin, (double*)fout, a, (cudaStream_t)stream); break;
+    case LBM_LAYOUT_PSOA: e = launch_step_layout<LBM_LAYOUT_PSOA>((const double*)fin, (double*)fout, a, (cudaStream_t)stream); break;
+    case LBM_LAYOUT_CAOSOA: e = launch_step_layout<LBM_LAYOUT_CAOSOA>((const double*)fin, (double*)fout, a, (cudaStream_t)stream); break;
     default: return LBM_EINVAL;
   }
   return e == cudaSuccess ? LBM_OK : LBM_ECUDA;

@@ -163,6 +163,13 @@ int32_t lbm_propagate(const lbm_params* p, const void* fin, void* ftmp, void* st
   return cuda_status(launch_propagate_fp64((const double*)fin, (double*)ftmp, a, as_stream(stream)));
 }
 
+int32_t lbm_propagate_push(const lbm_params* p, const void* fin, void* ftmp, void* stream) {
+  if (!params_ok(p) || !aligned16(fin) || !aligned16(ftmp) || p->precision != LBM_FP64) return LBM_EINVAL;
+  if (overlap(fin, ftmp, state_bytes(p))) return LBM_EINVAL;
+  const StepArgs a = make_args(p);
+  return cuda_status(launch_propagate_push_fp64((const double*)fin, (double*)ftmp, a, as_stream(stream)));
+}
+
 int32_t lbm_bc(const lbm_params* p, const void* fin, void* ftmp, void* stream) {
   if (!params_ok(p) || !aligned16(fin) || !aligned16(ftmp) || p->precision != LBM_FP64) return LBM_EINVAL;
   if (overlap(fin, ftmp, state_bytes(p))) return LBM_EINVAL;

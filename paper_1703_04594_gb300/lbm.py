@@ -75,6 +75,7 @@ _SIGS = {
     "lbm_step": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_run": (ctypes.c_int32, [_PP, _VP, _VP, ctypes.c_int32, _VP]),
     "lbm_propagate": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
+    "lbm_propagate_push": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_bc": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_collide": (ctypes.c_int32, [_PP, _VP, _VP, _VP]),
     "lbm_moments": (ctypes.c_int32, [_PP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -217,6 +218,12 @@ def propagate(p: Params, f_in, f_tmp, stream=None):
     return f_tmp
 
 
+def propagate_push(p: Params, f_in, f_tmp, stream=None):
+    _check("lbm_propagate_push", _lib().lbm_propagate_push(ctypes.byref(p.c()), _state(p, f_in, "f_in"),
+                                                           _state(p, f_tmp, "f_tmp"), _stream(stream)))
+    return f_tmp
+
+
 def bc(p: Params, f_in, f_tmp, stream=None):
     _check("lbm_bc", _lib().lbm_bc(ctypes.byref(p.c()), _state(p, f_in, "f_in"), _state(p, f_tmp, "f_tmp"),
                                    _stream(stream)))
@@ -286,7 +293,7 @@ def simulate_host(p: Params, fields_in, n_steps: int, fields_out, f_a, f_b, fiel
 
 
 # ------------------------------------------------------------------------- layouts
-LAYOUT_SOA, LAYOUT_AOS, LAYOUT_CSOA = 0, 1, 2
+LAYOUT_SOA, LAYOUT_AOS, LAYOUT_PSOA, LAYOUT_CAOSOA = 0, 1, 2, 3
 
 
 def convert_layout(p: Params, src, frm: int, dst, to: int, stream=None):

@@ -39,13 +39,16 @@ def test_init_matches_oracle():
     assert rel_err(to_host(p, f), OL.init_equilibrium(*fields)) <= KERNEL_TOL
 
 
+@pytest.mark.parametrize("form", ["pull", "push"])
 @pytest.mark.parametrize("bc", [lbm.BC_WALLS, lbm.BC_PERIODIC_Y])
-def test_propagate_bit_exact(bc):
-    p = lbm.Params(37, 45, bc=bc)
+@pytest.mark.parametrize("lx,ly", [(37, 45), (5, 7), (130, 70)])
+def test_propagate_bit_exact(form, bc, lx, ly):
+    """Pull (gather) and push (scatter) forms of propagate, Sec. 4: the same copy."""
+    p = lbm.Params(lx, ly, bc=bc)
     f = device_init(p, rt_fields(p, seed=3))
     tmp = lbm.empty_state(p)
     tmp.fill_(float("nan"))
-    lbm.propagate(p, f, tmp)
+    (lbm.propagate if form == "pull" else lbm.propagate_push)(p, f, tmp)
     got = to_host(p, tmp)
     want = OL.propagate(to_host(p, f), oracle_params(p))
     # entries with a source inside the fluid are pure copies: bit-exact
@@ -85,6 +88,17 @@ def test_separate_kernels_equal_fused_step():
     f = device_init(p, rt_fields(p, seed=6))
     tmp, a, b = lbm.empty_state(p), lbm.empty_state(p), lbm.empty_state(p)
     lbm.propagate(p, f, tmp)
+    lbm.bc(p, f, tmp)
+    lbm.collide(p, tmp, a)
+    lbm.step(p, f, b)
+    assert rel_err(to_host(p, a), to_host(p, b)) <= COLLIDE_TOL
+
+
+def test_push_propagate_step_equals_fused_step():
+    p = lbm.Params(64, 96, gx=1e-4)
+    f = device_init(p, rt_fields(p, seed=7))
+    tmp, a, b = lbm.empty_state(p), lbm.empty_state(p), lbm.empty_state(p)
+    lbm.propagate_push(p, f, tmp)
     lbm.bc(p, f, tmp)
     lbm.collide(p, tmp, a)
     lbm.step(p, f, b)
