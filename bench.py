@@ -65,8 +65,9 @@ def _args():
     ap.add_argument("--variant", choices=["fused", "separate", "push", "aos", "psoa", "caosoa"], default="fused",
                     help="fused SoA step; separate propagate/bc/collide kernels with the pull or push "
                          "propagate; fused step in the AoS, partitioned-SoA or CAoSoA layout (FP64)")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
-                    help="fp32 = FP32 shifted-deviation storage (fused only)")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp64fix"], default="fp64",
+                    help="fp32 = FP32 shifted-deviation storage (fused only); fp64fix = float64 storage "
+                         "with the fixed-point relaxation (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
                     help="batch = 256 independent lattices of uneven sizes; adjoint = gradient of the "
@@ -208,10 +209,11 @@ def run_ours(a):
 
     lx, ly = a.lx, a.ly
     fp32 = a.precision == "fp32"
-    if fp32 and a.variant != "fused":
-        raise SystemExit("--precision fp32 supports the fused step only")
+    fix = a.precision == "fp64fix"
+    if (fp32 or fix) and a.variant != "fused":
+        raise SystemExit(f"--precision {a.precision} supports the fused step only")
     p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
-                   precision=lbm.FP32_SHIFTED if fp32 else lbm.FP64)
+                   precision=lbm.FP32_SHIFTED if fp32 else (lbm.FP64_FIXED if fix else lbm.FP64))
     sites = lx * ly
     fields = I.rt_state(lx, ly, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))
     dev = [t.contiguous().cuda() for t in fields]
@@ -263,11 +265,12 @@ def run_ours(a):
 
     # dominant kernel: the fused step is the only launch of a fused bench step
     kern_ms = statistics.mean(per_step)
-    if fp32:
-        achieved = BYTES_PER_SITE_FP32 * sites / (kern_ms * 1e-3) / 1e9
+    if fp32 or fix:
+        achieved = (BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64) * sites / (kern_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": achieved / HBM_PEAK_GBS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get("fp32"),
-                    "kernel": "k_step_fp32", "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                    "frac": achieved / HBM_PEAK_GBS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(a.precision),
+                    "kernel": "k_step_fp32" if fp32 else "k_step_fix64",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     else:
         achieved = FLOPS_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -316,8 +319,10 @@ def run_ours(a):
     if rank == 0:
         line = {"metric": "D2Q37 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+i64+f64" if fp32 else "f64", "data": "synthetic",
-                "config": {"workload": f"D2Q37 {'FP32-shifted' if fp32 else 'FP64'} {a.variant} step, "
+                "vs_baseline": None, "dtype": "f32+i64+f64" if fp32 else ("f64+i64" if fix else "f64"),
+                "data": "synthetic",
+                "config": {"workload": f"D2Q37 {'FP32-shifted' if fp32 else ('FP64 fixed-point-relax' if fix else 'FP64')} "
+                                       f"{a.variant} step, "
                                        f"{lx}x{ly} Rayleigh-Taylor lattice",
                            "lx": lx, "ly": ly, "tau": TAU, "gy": GY, "t_bottom": T_BOTTOM, "t_top": T_TOP,
                            "seed": SEED, "variant": a.variant,

@@ -45,7 +45,15 @@ extern "C" {
 #endif
 
 enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, LBM_ENOMEM = 4, LBM_ESIZE = 5 };
-enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
+/* LBM_FP64: float64 populations, float64 collision arithmetic (moment sums in exact 64-bit
+ * fixed point).  LBM_FP32_SHIFTED: float32 storage of f_i - w_i rho0.  LBM_FP64_FIXED:
+ * float64 populations as LBM_FP64 (same buffers, interchangeable states); the fused step
+ * evaluates the equilibrium polynomial and the relaxation of every population in 64-bit
+ * fixed point on the integer pipes, with errors below one float64 rounding unit, for sites
+ * in a stated physical range (float64 elsewhere).  lbm_step, lbm_run, lbm_init, lbm_moments,
+ * lbm_kinetic_energy* and lbm_simulate_host accept it; the separate kernels, layouts,
+ * adjoint and batch entry points take LBM_FP64. */
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_FIXED = 2 };
 enum lbm_bc { LBM_BC_WALLS = 0, LBM_BC_PERIODIC_Y = 1 /* test mode: y wraps like x */ };
 
 /* Problem parameters, as the paper states the problem (Sec. 3): lattice size, BGK

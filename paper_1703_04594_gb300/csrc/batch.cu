@@ -308,6 +308,7 @@ extern "C" {
 
 int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* f_b, int32_t n, lbm_batch** out) {
   if (!params || !f_a || !f_b || !out || n <= 0 || n > 65535) return LBM_EINVAL;
+  if (params[0].precision != LBM_FP64 && params[0].precision != LBM_FP32_SHIFTED) return LBM_EINVAL;
   *out = nullptr;
   lbm_batch* b = new lbm_batch();
   b->n = n;

@@ -1,0 +1,127 @@
+// FP64 collision with the equilibrium polynomial and the relaxation in 64-bit fixed point.
+//
+// The same update as collide_site (Sec. 3, eq. "lbequation"; equilibrium and moments as in
+// collide_fp64.cuh), with a different split of the work between the GPU's pipes.  The site
+// scalars (moments, 1/rho, u, T, the gravity shift) and the per-shell Horner coefficients
+// stay in float64.  The per-population part, 8 of every 9 float64 operations of a site in
+// collide_site, runs in signed 64-bit fixed point on the integer pipes: for each opposite
+// pair, s = xi . u_s, s^2, the even part E = K0 + s^2 (K2 + K4 s^2), the odd part
+// O = s (K1 + K3 s^2) and f_+/- ' = (1 - omega) f_+/- + E +/- O.
+//
+// Formats.  Shell s is scaled by 2^e_s with w_s 2^e_s in [0.5, 1), so every scaled
+// population and coefficient is of order rho whatever the weight: values are signed
+// Q5.58 (resolution 2^-58, |v| < 32), s and 1 - omega are signed Q1.62, K3 and K4 unsigned
+// Q3.61.  The shell coefficients are formed in fixed point too, from omega rho times the
+// float64 Hermite coefficients and exact compile-time shell constants.  A product keeps the high 64 bits of the 128-bit result, a truncation that is
+// re-centred by adding half of the dropped unit.  Each output carries a few units of
+// 2^-58 relative to its scaled size, below the 2^-53 rounding unit of a float64 result.
+//
+// Range.  The path is taken for sites with |f_i| 2^e_s < 8 for all i, 0 < omega rho < 3,
+// |c u_s,x| and |c u_s,y| below 0.2 (so |s| < 0.8) and |T_s - 1| < 0.25; then every
+// intermediate stays below 27 in magnitude.  All other sites (and NaNs) take the float64
+// relaxation of collide_site, so results never depend on the range.
+#pragma once
+#include "collide_fp64.cuh"
+#include "fixed64.cuh"
+
+namespace d2q37 {
+
+__host__ __device__ constexpr int shell_exp(int s) {
+  constexpr int t[8] = {2, 3, 4, 6, 7, 9, 11, 11};
+  return t[s];
+}
+
+constexpr int FV = 58;  // scaled values: signed Q5.58
+constexpr int FU = 62;  // s, 1 - omega: signed Q1.62
+
+// Compile-time fixed-point constants from the model's float64 constants, computed exactly
+// in integers: a positive double is m 2^x with an integer m < 2^53.
+struct DoubleParts {
+  unsigned long long m;
+  int x;
+};
+__host__ __device__ constexpr DoubleParts double_parts(double v) {  // v > 0, finite
+  int x = 0;
+  while (v >= 9007199254740992.0) { v *= 0.5; ++x; }
+  while (v < 4503599627370496.0) { v *= 2.0; --x; }
+  return DoubleParts{(unsigned long long)v, x};
+}
+// round(a b 2^k / d) for positive doubles a, b and a positive integer d (half up); the
+// exact product of the two 53-bit significands fits 106 bits.
+__host__ __device__ constexpr unsigned long long fx_const(double a, double b, int k, unsigned d = 1) {
+  const DoubleParts pa = double_parts(a), pb = double_parts(b);
+  const unsigned __int128 p = (unsigned __int128)pa.m * pb.m;
+  const int sh = pa.x + pb.x + k;
+  const unsigned __int128 n = sh >= 0 ? (p << sh) : ((p + ((unsigned __int128)1 << (-sh - 1))) >> (-sh));
+  return (unsigned long long)((n + d / 2) / d);
+}
+// Shell constants with w' = w_s 2^e_s (signed formats need values below 2^63):
+//   cw = w' (Q0.63), cq = w' q_s (Q4.59), cq2 = w' q_s^2 (Q8.55, with q_s^2 rounded to
+//   64 bits first), cw6 = w' / 6 and cw24 = w' / 24 (unsigned Q0.64).
+__host__ __device__ constexpr long long shell_cw(int s) {
+  return (long long)fx_const(w_shell(s), 1.0, shell_exp(s) + 63);
+}
+__host__ __device__ constexpr long long shell_cq(int s) {
+  return (long long)fx_const(w_shell(s), q_shell(s), shell_exp(s) + 59);
+}
+__host__ __device__ constexpr long long shell_cq2(int s) {
+  // round(w' q q 2^55): the 106-bit product w' q is rounded to 64 significant bits, then
+  // multiplied by q exactly (117 bits)
+  const DoubleParts pw = double_parts(w_shell(s)), pq = double_parts(q_shell(s));
+  unsigned __int128 p = (unsigned __int128)pw.m * pq.m;
+  int x = pw.x + pq.x;
+  while (p >= ((unsigned __int128)1 << 64)) {
+    p = (p + 1) >> 1;
+    ++x;
+  }
+  const unsigned __int128 p3 = p * pq.m;
+  const int sh = x + pq.x + shell_exp(s) + 55;  // negative for every shell
+  return (long long)((p3 + ((unsigned __int128)1 << (-sh - 1))) >> (-sh));
+}
+__host__ __device__ constexpr unsigned long long shell_cw_div(int s, unsigned d) {
+  return fx_const(w_shell(s), 1.0, shell_exp(s) + 64, d);
+}
+
+// The tables, evaluated by the compiler (constexpr locals must be constant expressions), so
+// kernels only ever read literals.
+__host__ __device__ constexpr long long kCw(int s) {
+  constexpr long long t[8] = {shell_cw(0), shell_cw(1), shell_cw(2), shell_cw(3),
+                              shell_cw(4), shell_cw(5), shell_cw(6), shell_cw(7)};
+  return t[s];
+}
+__host__ __device__ constexpr long long kCq(int s) {
+  constexpr long long t[8] = {0, shell_cq(1), shell_cq(2), shell_cq(3), shell_cq(4), shell_cq(5), shell_cq(6),
+                              shell_cq(7)};
+  return t[s];
+}
+__host__ __device__ constexpr long long kCq2(int s) {
+  constexpr long long t[8] = {0,            shell_cq2(1), shell_cq2(2), shell_cq2(3),
+                              shell_cq2(4), shell_cq2(5), shell_cq2(6), shell_cq2(7)};
+  return t[s];
+}
+__host__ __device__ constexpr unsigned long long kCw6(int s) {
+  constexpr unsigned long long t[8] = {shell_cw_div(0, 6), shell_cw_div(1, 6), shell_cw_div(2, 6),
+                                       shell_cw_div(3, 6), shell_cw_div(4, 6), shell_cw_div(5, 6),
+                                       shell_cw_div(6, 6), shell_cw_div(7, 6)};
+  return t[s];
+}
+__host__ __device__ constexpr unsigned long long kCw24(int s) {
+  constexpr unsigned long long t[8] = {shell_cw_div(0, 24), shell_cw_div(1, 24), shell_cw_div(2, 24),
+                                       shell_cw_div(3, 24), shell_cw_div(4, 24), shell_cw_div(5, 24),
+                                       shell_cw_div(6, 24), shell_cw_div(7, 24)};
+  return t[s];
+}
+
+// Positive float64 values order like their bit patterns.
+constexpr long long kBitsR = 0x4008000000000000LL;  // 3.0
+constexpr long long kBitsU = 0x3FC999999999999ALL;  // 0.2
+constexpr long long kBitsT = 0x3FD0000000000000LL;  // 0.25
+constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL;
+
+__device__ __forceinline__ bool fixed_range_ok(const SiteScalars& v) {
+  const long long r = __double_as_longlong(v.R);
+  return r > 0 && r < kBitsR && (__double_as_longlong(v.Ux) & kAbs) < kBitsU &&
+         (__double_as_longlong(v.Uy) & kAbs) < kBitsU && (__double_as_longlong(v.t) & kAbs) < kBitsT;
+}
+
+}  // namespace d2q37

@@ -40,9 +40,10 @@ struct CollideConst {
 // Valid while sum_i |v_i|^2 |f_i| < 2048 (physical states: rho below ~200).
 constexpr int DFIX = 52;
 
-__device__ __forceinline__ long long to_fix52(double v) {
+// Also returns the biased exponent field E of v.
+__device__ __forceinline__ long long to_fix52_e(double v, int& E) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int E = (int)((b >> 52) & 0x7ffu);
+  E = (int)((b >> 52) & 0x7ffu);
   const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // 53-bit mantissa
   const int sh = E - 1023;  // v * 2^52 = m * 2^sh
   const int l = sh < 0 ? 0 : (sh < 10 ? sh : 10);   // left shift (|v| >= 1)
@@ -54,15 +55,27 @@ __device__ __forceinline__ long long to_fix52(double v) {
   return (x ^ s) - s;
 }
 
+__device__ __forceinline__ long long to_fix52(double v) {
+  int E;
+  return to_fix52_e(v, E);
+}
+
 // Streaming accumulation: each opposite pair is converted and added to the four sums
 // at once, so only the sums stay live (the products by the small integer velocity
-// weights are exact integer shifts and adds).
-__device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, double& jx, double& jy,
-                                            double& e) {
-  long long R = to_fix52(f[0]), Ei = 0, Jx = 0, Jy = 0;
+// weights are exact integer shifts and adds).  on_exp(i, E) sees the exponent field of
+// every f_i (for range checks of callers; a no-op otherwise).
+// `fget(i)` returns f_i (an array read, or a load); it is called once per population.
+template <class Fget, class OnExp>
+__device__ __forceinline__ void moments_get(Fget&& fget, double& rho, double& jx, double& jy, double& e,
+                                            OnExp&& on_exp) {
+  int E0, Ea, Eb;
+  long long R = to_fix52_e(fget(0), E0), Ei = 0, Jx = 0, Jy = 0;
+  on_exp(0, E0);
 #pragma unroll
   for (int k = 1; k <= NPAIR; ++k) {
-    const long long a = to_fix52(f[k]), b = to_fix52(f[k + NPAIR]);
+    const long long a = to_fix52_e(fget(k), Ea), b = to_fix52_e(fget(k + NPAIR), Eb);
+    on_exp(k, Ea);
+    on_exp(k + NPAIR, Eb);
     const long long P = a + b, M = a - b;
     R += P;
     Ei += (long long)v2(k) * P;
@@ -76,6 +89,10 @@ __device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, d
   jy = (double)Jy * S;
 }
 
+__device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, double& jx, double& jy, double& e) {
+  moments_get([&](int i) { return f[i]; }, rho, jx, jy, e, [](int, int) {});
+}
+
 // Equilibrium coefficients of one site.  R = omega * rho for a collision (the result is
 // omega f^eq), or rho for a plain equilibrium.  Outputs per shell s = 0..7 the Horner
 // coefficients K0..K4 of R w_s (C0 + C1 s + C2 s^2 + s^3/6 + s^4/24).
@@ -83,26 +100,41 @@ struct ShellCoef {
   double K0[8], K1[8], K2[8], K3[8], K4[8];
 };
 
-__device__ __forceinline__ void shell_coefficients(double R, double t, double U, ShellCoef& k) {
+// C0..C2 as polynomials in q: C0 = a00 + a01 q + a02 q^2, C1 = a10 + a11 q, C2 = a20 + a21 q.
+struct HermiteA {
+  double a00, a01, a02, a10, a11, a20, a21;
+};
+
+__device__ __forceinline__ HermiteA hermite_a(double t, double U) {
   const double tU = t * U, t2 = t * t;
-  const double a00 = fma(0.125, U * U, fma(-0.5, U, 1.0) - t) + (tU + t2);
-  const double a01 = fma(-0.25, tU, 0.5 * t) - t2;
-  const double a02 = 0.125 * t2;
-  const double a10 = fma(-0.5, U, 1.0) - 2.0 * t;
-  const double a11 = 0.5 * t;
-  const double a20 = fma(-0.25, U, 0.5) - 1.5 * t;
-  const double a21 = 0.25 * t;
-  k.K0[0] = (R * w_shell(0)) * a00;
+  HermiteA h;
+  h.a00 = fma(0.125, U * U, fma(-0.5, U, 1.0) - t) + (tU + t2);
+  h.a01 = fma(-0.25, tU, 0.5 * t) - t2;
+  h.a02 = 0.125 * t2;
+  h.a10 = fma(-0.5, U, 1.0) - 2.0 * t;
+  h.a11 = 0.5 * t;
+  h.a20 = fma(-0.25, U, 0.5) - 1.5 * t;
+  h.a21 = 0.25 * t;
+  return h;
+}
+
+// K0..K4 of shell s >= 1 (K0 only for s = 0).
+__device__ __forceinline__ void shell_coefficient(const HermiteA& h, double R, int s, double& K0, double& K1,
+                                                  double& K2, double& K3, double& K4) {
+  const double q = q_shell(s);
+  const double W = R * w_shell(s);
+  K0 = s == 0 ? W * h.a00 : W * fma(fma(h.a02, q, h.a01), q, h.a00);
+  K1 = W * fma(h.a11, q, h.a10);
+  K2 = W * fma(h.a21, q, h.a20);
+  K3 = W * (1.0 / 6.0);
+  K4 = W * (1.0 / 24.0);
+}
+
+__device__ __forceinline__ void shell_coefficients(double R, double t, double U, ShellCoef& k) {
+  const HermiteA h = hermite_a(t, U);
+  k.K0[0] = (R * w_shell(0)) * h.a00;
 #pragma unroll
-  for (int s = 1; s < 8; ++s) {
-    const double q = q_shell(s);
-    const double W = R * w_shell(s);
-    k.K0[s] = W * fma(fma(a02, q, a01), q, a00);
-    k.K1[s] = W * fma(a11, q, a10);
-    k.K2[s] = W * fma(a21, q, a20);
-    k.K3[s] = W * (1.0 / 6.0);
-    k.K4[s] = W * (1.0 / 24.0);
-  }
+  for (int s = 1; s < 8; ++s) shell_coefficient(h, R, s, k.K0[s], k.K1[s], k.K2[s], k.K3[s], k.K4[s]);
 }
 
 // s = v . (Ux, Uy) for integer v with |vx|, |vy| <= 3, from precomputed multiples.
@@ -124,14 +156,14 @@ __device__ __forceinline__ double dot_v(const Multiples& m, int vxk, int vyk) {
 
 // Relaxation: out_i = om1 * f_i + R w_i P_i(s_i), for a whole site.  With om1 = 0 and
 // R = rho this is the plain equilibrium.  `store(i, value)` receives each population.
-template <class Store>
-__device__ __forceinline__ void relax_site(const double (&f)[Q], double om1, double R, double Ux, double Uy,
-                                           double t, Store&& store) {
+template <class Fget, class Store>
+__device__ __forceinline__ void relax_site_get(Fget&& fget, double om1, double R, double Ux, double Uy, double t,
+                                               Store&& store) {
   const double U = fma(Ux, Ux, Uy * Uy) * (1.0 / C2);
   ShellCoef k;
   shell_coefficients(R, t, U, k);
   const Multiples m = make_multiples(Ux, Uy);
-  store(0, fma(om1, f[0], k.K0[0]));
+  store(0, fma(om1, fget(0), k.K0[0]));
 #pragma unroll
   for (int j = 1; j <= NPAIR; ++j) {
     const int sh = shell(j);
@@ -139,23 +171,49 @@ __device__ __forceinline__ void relax_site(const double (&f)[Q], double om1, dou
     const double s2 = s * s;
     const double E = fma(fma(k.K4[sh], s2, k.K2[sh]), s2, k.K0[sh]);
     const double O = s * fma(k.K3[sh], s2, k.K1[sh]);
-    store(j, fma(om1, f[j], E + O));
-    store(j + NPAIR, fma(om1, f[j + NPAIR], E - O));
+    store(j, fma(om1, fget(j), E + O));
+    store(j + NPAIR, fma(om1, fget(j + NPAIR), E - O));
   }
 }
 
-// Full collision of one site (moments -> gravity shift -> equilibrium -> BGK).
 template <class Store>
-__device__ __forceinline__ void collide_site(const double (&f)[Q], const CollideConst& cc, Store&& store) {
-  double rho, jx, jy, e;
-  moments_int(f, rho, jx, jy, e);
+__device__ __forceinline__ void relax_site(const double (&f)[Q], double om1, double R, double Ux, double Uy,
+                                           double t, Store&& store) {
+  relax_site_get([&](int i) { return f[i]; }, om1, R, Ux, Uy, t, store);
+}
+
+// Site scalars of the collision: R = omega rho, the gravity-shifted c u_s and t = T_s - 1.
+struct SiteScalars {
+  double R, Ux, Uy, t;
+};
+
+__device__ __forceinline__ SiteScalars scalars_from_moments(double rho, double jx, double jy, double e,
+                                                          const CollideConst& cc) {
   const double inv_rho = 1.0 / rho;
   const double c2ir = C2 * inv_rho;
   const double Ux0 = jx * c2ir, Uy0 = jy * c2ir;              // c * u
   const double uu = fma(Ux0, Ux0, Uy0 * Uy0) * (1.0 / C2);     // |u|^2
   const double TD = fma(e, c2ir, -uu);                         // D T
-  const double t = fma(TD, 1.0 / D, cc.tshift);                // T_s - 1
-  relax_site(f, cc.om1, cc.omega * rho, Ux0 + cc.cgx, Uy0 + cc.cgy, t, store);
+  SiteScalars r;
+  r.t = fma(TD, 1.0 / D, cc.tshift);                           // T_s - 1
+  r.R = cc.omega * rho;
+  r.Ux = Ux0 + cc.cgx;
+  r.Uy = Uy0 + cc.cgy;
+  return r;
+}
+
+template <class Fget, class OnExp>
+__device__ __forceinline__ SiteScalars site_scalars(Fget&& fget, const CollideConst& cc, OnExp&& on_exp) {
+  double rho, jx, jy, e;
+  moments_get(fget, rho, jx, jy, e, on_exp);
+  return scalars_from_moments(rho, jx, jy, e, cc);
+}
+
+// Full collision of one site (moments -> gravity shift -> equilibrium -> BGK).
+template <class Store>
+__device__ __forceinline__ void collide_site(const double (&f)[Q], const CollideConst& cc, Store&& store) {
+  const SiteScalars v = site_scalars([&](int i) { return f[i]; }, cc, [](int, int) {});
+  relax_site(f, cc.om1, v.R, v.Ux, v.Uy, v.t, store);
 }
 
 }  // namespace d2q37

@@ -1,0 +1,79 @@
+// 64-bit fixed-point arithmetic on the integer pipes.
+//
+// GB300 executes float64 at 2 operations per clock per SM, 1/64 of its float32 rate, while
+// its integer pipes issue 64 operations per clock per SM.  A signed or unsigned 64 x 64 ->
+// high-64 product (a handful of IMAD instructions) then costs a fraction of one DFMA.  The
+// helpers below move values between float64 and signed 64-bit fixed point (value = X * 2^-k)
+// with integer instructions only, so no float64 conversion instruction is issued either.
+#pragma once
+#include <stdint.h>
+
+namespace d2q37 {
+
+// round(v * 2^k) for a float64 v, as a signed 64-bit integer; integer instructions only.
+// v * 2^k = m * 2^sh with m the 53-bit significand.  Left shifts (sh >= 0) are exact;
+// right shifts round half up.  `ovf` is set when sh > max_sh, i.e. when |v| * 2^k may
+// reach 2^(53 + max_sh); the caller picks max_sh so that its format cannot overflow.
+// Zeros and subnormals give 0.
+__host__ __device__ __forceinline__ long long fx_from_double(double v, int k, int max_sh, bool& ovf) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &v, 8);
+#endif
+  const int E = (int)((b >> 52) & 0x7ffu);
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int sh = E - 1075 + k;
+  ovf |= sh > max_sh;
+  const int l = sh < 0 ? 0 : (sh < 10 ? sh : 10);
+  const int r = sh < 0 ? (-sh < 62 ? -sh : 62) : 0;
+  const long long half = r > 0 ? (1LL << (r - 1)) : 0;
+  long long x = ((m + half) >> r) << l;
+  x = E == 0 ? 0 : x;
+  const long long s = (long long)b >> 63;  // 0 or -1
+  return (x ^ s) - s;
+}
+
+// X * 2^-k as a float64, rounded half up in magnitude; integer instructions only.
+// Valid for 0 < 1086 - clz(|X|) - k < 2047 (normal results), which holds for every use here.
+__host__ __device__ __forceinline__ double fx_to_double(long long X, int k) {
+  const long long s = X >> 63;
+  const unsigned long long A = (unsigned long long)((X ^ s) - s);
+#ifdef __CUDA_ARCH__
+  const int lz = __clzll((long long)A);
+#else
+  const int lz = A ? __builtin_clzll(A) : 64;
+#endif
+  const unsigned long long M = A << (lz & 63);
+  const unsigned long long mant = ((M >> 10) + 1) >> 1;  // 53 bits, may carry to 2^53
+  const unsigned long long e = (unsigned long long)(1086 - lz - k - 1);
+  unsigned long long bits = (e << 52) + mant;
+  bits |= (unsigned long long)s & 0x8000000000000000ull;
+  bits = A == 0 ? 0ull : bits;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double d;
+  __builtin_memcpy(&d, &bits, 8);
+  return d;
+#endif
+}
+
+// High 64 bits of the 128-bit products.
+__host__ __device__ __forceinline__ long long fx_mulhi(long long a, long long b) {
+#ifdef __CUDA_ARCH__
+  return __mul64hi(a, b);
+#else
+  return (long long)(((__int128)a * (__int128)b) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long fx_umulhi(unsigned long long a, unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (unsigned long long)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+#endif
+}
+
+}  // namespace d2q37

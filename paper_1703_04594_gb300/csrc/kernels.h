@@ -33,6 +33,7 @@ struct StepWalls {
 struct StepArgs : StepScalars, StepWalls {};
 
 cudaError_t launch_step_fp64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fix64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_propagate_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_propagate_push_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_bc_fp64(const double* fin, double* ftmp, const StepArgs& a, cudaStream_t s);

@@ -9,7 +9,7 @@
 #include <stdint.h>
 
 #include "kernels.h"
-#include "step_fp64.cuh"
+#include "step_fix64.cuh"
 
 namespace d2q37 {
 
@@ -35,6 +35,19 @@ __global__ void __launch_bounds__(128, 4) k_step_fp64(const double* __restrict__
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp
   step_strip_fp64<PERIODIC>(fin, fout, a, a, x, blockIdx.x * 32, LdReadOnly());
+}
+
+// The same fused step with the fixed-point relaxation of collide_fix64.cuh.
+#ifndef LBM_FIX64_MIN_BLOCKS
+#define LBM_FIX64_MIN_BLOCKS 6
+#endif
+template <bool PERIODIC>
+__global__ void __launch_bounds__(128, LBM_FIX64_MIN_BLOCKS) k_step_fix64(const double* __restrict__ fin,
+                                                                         double* __restrict__ fout, StepArgs a) {
+  __shared__ double staged[kFixWarps][Q * 32];  // 37 populations x 32 sites per warp
+  const int x = blockIdx.y * 4 + threadIdx.y;
+  if (x >= a.lx) return;  // uniform per warp
+  step_strip_fix64<PERIODIC>(fin, fout, a, a, x, blockIdx.x * 32, LdReadOnly(), staged[threadIdx.y]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -203,6 +216,12 @@ static const dim3 kSiteBlock(32, 4);
 cudaError_t launch_step_fp64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s) {
   if (a.periodic) k_step_fp64<true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
   else k_step_fp64<false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_fix64(const double* fin, double* fout, const StepArgs& a, cudaStream_t s) {
+  if (a.periodic) k_step_fix64<true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+  else k_step_fix64<false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
   return cudaGetLastError();
 }
 

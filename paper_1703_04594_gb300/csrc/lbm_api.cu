@@ -25,7 +25,8 @@ bool d2q37::params_valid(const lbm_params* p) {
   if (!p) return false;
   if (p->lx < 4 || p->ly < 6) return false;
   if (!(p->tau > 0.5) || !(p->tau < 1e6)) return false;
-  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED) return false;
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED && p->precision != LBM_FP64_FIXED)
+    return false;
   if (p->bc != LBM_BC_WALLS && p->bc != LBM_BC_PERIODIC_Y) return false;
   // grid.y = ceil(lx / 4) must fit in 65535; 37 * lx * pitch must fit the index math
   if (p->lx > 4 * 65535) return false;
@@ -45,7 +46,7 @@ namespace {
 bool params_ok(const lbm_params* p) { return params_valid(p); }
 
 int64_t pitch_of(const lbm_params* p) { return ((int64_t)p->ly + 31) / 32 * 32; }
-int64_t elem_size(const lbm_params* p) { return p->precision == LBM_FP64 ? 8 : 4; }
+int64_t elem_size(const lbm_params* p) { return p->precision == LBM_FP32_SHIFTED ? 4 : 8; }
 int64_t state_bytes(const lbm_params* p) { return (int64_t)Q * p->lx * pitch_of(p) * elem_size(p); }
 
 bool aligned16(const void* ptr) { return ptr && ((uintptr_t)ptr % 16) == 0; }
@@ -97,6 +98,7 @@ StepArgs d2q37::make_step_args(const lbm_params* p) {
 
 cudaError_t d2q37::launch_step(const void* fin, void* fout, const StepArgs& a, int32_t precision, cudaStream_t s) {
   if (precision == LBM_FP32_SHIFTED) return launch_step_fp32((const float*)fin, (float*)fout, a, s);
+  if (precision == LBM_FP64_FIXED) return launch_step_fix64((const double*)fin, (double*)fout, a, s);
   return launch_step_fp64((const double*)fin, (double*)fout, a, s);
 }
 

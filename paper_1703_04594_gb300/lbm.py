@@ -16,7 +16,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_native", "liblbm_d2q37.so")
 
-FP64, FP32_SHIFTED = 0, 1
+FP64, FP32_SHIFTED, FP64_FIXED = 0, 1, 2
 BC_WALLS, BC_PERIODIC_Y = 0, 1
 Q = 37
 
@@ -169,7 +169,7 @@ def buffer_bytes(p: Params) -> int:
 
 
 def state_dtype(p: Params):
-    return torch.float64 if p.precision == FP64 else torch.float32
+    return torch.float32 if p.precision == FP32_SHIFTED else torch.float64
 
 
 def empty_state(p: Params, device="cuda") -> torch.Tensor:
