@@ -2,24 +2,28 @@
 //
 // The same update as collide_site (Sec. 3, eq. "lbequation"; equilibrium and moments as in
 // collide_fp64.cuh), with a different split of the work between the GPU's pipes.  The site
-// scalars (moments, 1/rho, u, T, the gravity shift) and the per-shell Horner coefficients
-// stay in float64.  The per-population part, 8 of every 9 float64 operations of a site in
-// collide_site, runs in signed 64-bit fixed point on the integer pipes: for each opposite
-// pair, s = xi . u_s, s^2, the even part E = K0 + s^2 (K2 + K4 s^2), the odd part
-// O = s (K1 + K3 s^2) and f_+/- ' = (1 - omega) f_+/- + E +/- O.
+// scalars (moments, 1/rho, u, T, the gravity shift, the Hermite coefficients a_jk) stay in
+// float64.  Everything per shell and per population runs in signed 64-bit fixed point on
+// the integer pipes: the shell coefficients K0..K4 of omega rho w_s (C0 + C1 s + C2 s^2 +
+// s^3/6 + s^4/24), and for each opposite pair s = xi . u_s, s^2, the even part
+// E = K0 + s^2 (K2 + K4 s^2), the odd part O = s (K1 + K3 s^2) and
+// f_+/-' = (1 - omega) f_+/- + E +/- O.
 //
 // Formats.  Shell s is scaled by 2^e_s with w_s 2^e_s in [0.5, 1), so every scaled
-// population and coefficient is of order rho whatever the weight: values are signed
-// Q5.58 (resolution 2^-58, |v| < 32), s and 1 - omega are signed Q1.62, K3 and K4 unsigned
-// Q3.61.  The shell coefficients are formed in fixed point too, from omega rho times the
-// float64 Hermite coefficients and exact compile-time shell constants.  A product keeps the high 64 bits of the 128-bit result, a truncation that is
-// re-centred by adding half of the dropped unit.  Each output carries a few units of
-// 2^-58 relative to its scaled size, below the 2^-53 rounding unit of a float64 result.
+// population and coefficient is of order rho whatever the weight.  A product keeps the
+// high 64 bits of the 128-bit result (a truncation).  Each quantity has the number of
+// fraction bits that makes every product land on its consumer's binary point with no
+// shift: outputs, E, O and K0 have 58 (|v| < 32), K1 and 1 - omega times f 59 and 63,
+// K2 60, K3 61, K4 62, s 63 and s^2 62.  Each output carries a few units of 2^-58 relative
+// to its scaled size, below the 2^-53 rounding unit of a float64 result.  The truncations
+// (each -1/2 unit on average) are re-centred by small constant offsets to within half a
+// unit of 2^-58, far below the systematic error that the float64 weights themselves put on
+// mass conservation.
 //
-// Range.  The path is taken for sites with |f_i| 2^e_s < 8 for all i, 0 < omega rho < 3,
-// |c u_s,x| and |c u_s,y| below 0.2 (so |s| < 0.8) and |T_s - 1| < 0.25; then every
-// intermediate stays below 27 in magnitude.  All other sites (and NaNs) take the float64
-// relaxation of collide_site, so results never depend on the range.
+// Range.  The path is taken for sites with 0 <= f_i 2^e_s < 8 for all i,
+// 0 < omega rho < 3, |c u_s,x| and |c u_s,y| below 0.15 (so |s| < 0.6) and
+// |T_s - 1| < 0.25; then every intermediate stays inside its format.  All other sites (and
+// NaNs) take the float64 collision of collide_site, so results never depend on the range.
 #pragma once
 #include "collide_fp64.cuh"
 #include "fixed64.cuh"
@@ -114,7 +118,7 @@ __host__ __device__ constexpr unsigned long long kCw24(int s) {
 
 // Positive float64 values order like their bit patterns.
 constexpr long long kBitsR = 0x4008000000000000LL;  // 3.0
-constexpr long long kBitsU = 0x3FC999999999999ALL;  // 0.2
+constexpr long long kBitsU = 0x3FC3333333333333LL;  // 0.15
 constexpr long long kBitsT = 0x3FD0000000000000LL;  // 0.25
 constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL;
 

@@ -50,7 +50,9 @@ __host__ __device__ __forceinline__ double fx_to_double(long long X, int k) {
   const unsigned long long e = (unsigned long long)(1086 - lz - k - 1);
   unsigned long long bits = (e << 52) + mant;
   bits |= (unsigned long long)s & 0x8000000000000000ull;
+#ifndef LBM_FX_NO_ZERO_CHECK
   bits = A == 0 ? 0ull : bits;
+#endif
 #ifdef __CUDA_ARCH__
   return __longlong_as_double((long long)bits);
 #else
@@ -58,6 +60,14 @@ __host__ __device__ __forceinline__ double fx_to_double(long long X, int k) {
   __builtin_memcpy(&d, &bits, 8);
   return d;
 #endif
+}
+
+// X * 2^-k through the float64 pipe: one I2F (exact round to nearest) and an integer
+// subtraction from the exponent field.  Valid for normal results; 0 stays 0.  Used to move
+// part of the conversion work from the integer pipes to the otherwise idle float64 pipe.
+__device__ __forceinline__ double fx_to_double_dp(long long X, int k) {
+  const long long b = __double_as_longlong(__ll2double_rn(X)) - ((long long)k << 52);
+  return X == 0 ? 0.0 : __longlong_as_double(b);
 }
 
 // High 64 bits of the 128-bit products.
@@ -74,6 +84,12 @@ __host__ __device__ __forceinline__ unsigned long long fx_umulhi(unsigned long l
 #else
   return (unsigned long long)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
 #endif
+}
+// Signed a times b with 0 <= b < 2^63: the unsigned product of a's bit pattern is
+// (a + 2^64) b when a < 0, whose high half exceeds that of a b by exactly b.
+__host__ __device__ __forceinline__ long long fx_mulhi_su(long long a, unsigned long long b) {
+  const unsigned long long h = fx_umulhi((unsigned long long)a, b);
+  return (long long)(a < 0 ? h - b : h);
 }
 
 }  // namespace d2q37

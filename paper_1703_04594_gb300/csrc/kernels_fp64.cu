@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128, 4) k_step_fp64(const double* __restrict__
 
 // The same fused step with the fixed-point relaxation of collide_fix64.cuh.
 #ifndef LBM_FIX64_MIN_BLOCKS
-#define LBM_FIX64_MIN_BLOCKS 6
+#define LBM_FIX64_MIN_BLOCKS 5
 #endif
 template <bool PERIODIC>
 __global__ void __launch_bounds__(128, LBM_FIX64_MIN_BLOCKS) k_step_fix64(const double* __restrict__ fin,

@@ -68,8 +68,45 @@ __device__ __forceinline__ void cp_async8(double* smem_dst, const double* gmem_s
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Conversion of the second population of each pair back to float64: on the integer pipes
+// (fx_to_double) or through the float64 pipe (fx_to_double_dp), whichever balances the
+// kernel's pipes better.
+#ifndef LBM_FIX64_TO_DOUBLE_MINUS
+#define LBM_FIX64_TO_DOUBLE_MINUS fx_to_double_dp
+#endif
+#ifndef LBM_FIX64_TO_DOUBLE_PLUS
+#define LBM_FIX64_TO_DOUBLE_PLUS fx_to_double
+#endif
+
 // Shared staging: one warp holds sf[i * 32 + lane] for its 32 sites.
 constexpr int kFixWarps = 4;  // warps per block (block = 32 x 4 threads)
+
+// Pull-gather address of population i for the lane's row yc (interior warps).
+template <bool PERIODIC>
+__device__ __forceinline__ const double* gather_src(const double* fin, const StepScalars& a, int x, int yc, int i) {
+  const long long col = (long long)wrap_index(x - vx(i), a.lx) * a.pitch;
+  const int ys = PERIODIC ? wrap_index(yc - vy(i), a.ly) : yc - vy(i);
+  return fin + i * a.pop + col + ys;
+}
+
+// The float64 collision of one interior site on values loaded again from global memory:
+// the path of sites outside the fixed-point range.  Not inlined, so that its 37 live
+// float64 values do not weigh on the register allocation of the fixed-point path.
+template <bool PERIODIC>
+__device__ __noinline__ void collide_site_reloaded(const double* __restrict__ fin, double* __restrict__ fout,
+                                                   const StepScalars& a, int x, int yc, unsigned self) {
+  double f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = __ldg(gather_src<PERIODIC>(fin, a, x, yc, i));
+  collide_site(f, a.cc, [&](int i, double val) { __stcs(fout + i * a.pop + self, val); });
+}
+
+// The float64 strip of a warp next to a wall, not inlined for the same reason.
+template <bool PERIODIC>
+__device__ __noinline__ void wall_strip_fp64(const double* __restrict__ fin, double* __restrict__ fout,
+                                             const StepScalars& a, const StepWalls& w, int x, int y0) {
+  step_strip_fp64<PERIODIC>(fin, fout, a, w, x, y0, LdReadOnly());
+}
 
 template <bool PERIODIC, class Ld>
 __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin, double* __restrict__ fout,
@@ -77,7 +114,7 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
                                                  double* __restrict__ sf) {
   const bool wall_warp = !PERIODIC && (y0 < 3 || y0 + 32 > a.ly - 3);
   if (wall_warp) {
-    step_strip_fp64<PERIODIC>(fin, fout, a, w, x, y0, ld);
+    wall_strip_fp64<PERIODIC>(fin, fout, a, w, x, y0);
     return;
   }
   const int lane = threadIdx.x & 31;
@@ -99,61 +136,76 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     __syncwarp();
   }
   sf += lane;
-  // 2. moments in 64-bit fixed point, with the range check of the fixed-point path
-  constexpr double S = 1.0 / 4503599627370496.0;  // 2^-52
-  int E;
-  long long R = to_fix52_e(sf[0], E), Ei = 0, Jx = 0, Jy = 0;
-  bool out = E > 1025 - shell_exp(0);
-  unsigned sign = (unsigned)(__double_as_longlong(sf[0]) >> 32);
+  long long* const sx = reinterpret_cast<long long*>(sf);  // the same slots, as fixed point
+  // 2. every population to fixed point f' = f 2^(59 + e_s), written back in place, and the
+  //    moments from f' rounded to 2^-56: rho, j and sum |v|^2 f stay below 2^4 there for
+  //    every state in range.  The exponent field of a population in range is at most
+  //    1025 - e_s; a negative one has the sign bit set, so one unsigned compare flags both.
+  constexpr double S = 1.0 / 72057594037927936.0;  // 2^-56
+  bool out;
+  long long R, Ei = 0, Jx = 0, Jy = 0;
+  {
+    constexpr int e = shell_exp(0);
+    const double f0 = sf[0];
+    out = (unsigned long long)__double_as_longlong(f0) >> 52 > 1025 - e;
+    const long long q0 = fx_from_nonneg(f0, 59 + e);
+    sx[0] = q0;
+    R = (q0 + (1LL << (2 + e))) >> (3 + e);
+  }
 #pragma unroll 1
   for (int k = 1; k <= NPAIR; ++k) {
     const int vxk = (int)((kPairVx >> (2 * (k - 1))) & 3);
     const int vyk = (int)((kPairVy >> (3 * (k - 1))) & 7) - 3;
-    const int lim = c_shell_fix[(kPairShell >> (3 * (k - 1))) & 7].lim;
+    const ShellFix& c = c_shell_fix[(kPairShell >> (3 * (k - 1))) & 7];
     const double fa = sf[k * 32], fb = sf[(k + NPAIR) * 32];
-    int Ea, Eb;
-    const long long va = to_fix52_e(fa, Ea), vb = to_fix52_e(fb, Eb);
-    out |= (Ea > lim) | (Eb > lim);
-    sign |= (unsigned)(__double_as_longlong(fa) >> 32) | (unsigned)(__double_as_longlong(fb) >> 32);
+    out |= ((unsigned long long)__double_as_longlong(fa) >> 52 > (unsigned)c.lim) |
+           ((unsigned long long)__double_as_longlong(fb) >> 52 > (unsigned)c.lim);
+    const long long qa = fx_from_nonneg(fa, 59 + c.e), qb = fx_from_nonneg(fb, 59 + c.e);
+    sx[k * 32] = qa;
+    sx[(k + NPAIR) * 32] = qb;
+    const int sh = 3 + c.e;
+    const long long half = 1LL << (sh - 1);
+    const long long va = (qa + half) >> sh, vb = (qb + half) >> sh;
     const long long P = va + vb, M = va - vb;
     R += P;
     Ei += (long long)(vxk * vxk + vyk * vyk) * P;
     Jx += (long long)vxk * M;
     Jy += (long long)vyk * M;
   }
-  out |= (sign >> 31) != 0;  // a negative population
   if (!active) return;
-  // 3. site scalars in float64
-  const SiteScalars v = scalars_from_moments((double)R * S, (double)Jx * S, (double)Jy * S, (double)Ei * S, a.cc);
   const unsigned self = (unsigned)((long long)x * a.pitch + y);
   const auto store = [&](int i, double val) { __stcs(fout + i * a.pop + self, val); };
+  // 3. site scalars in float64; sites out of range (negative or large populations, fast or
+  //    hot fluid) take the float64 collision
+  const SiteScalars v = scalars_from_moments((double)R * S, (double)Jx * S, (double)Jy * S, (double)Ei * S, a.cc);
   if (out || !fixed_range_ok(v)) {
-    relax_site_get([&](int i) { return sf[i * 32]; }, a.cc.om1, v.R, v.Ux, v.Uy, v.t, store);
+    collide_site_reloaded<PERIODIC>(fin, fout, a, x, yc, self);
     return;
   }
   // 4. fixed-point relaxation
   const double U = fma(v.Ux, v.Ux, v.Uy * v.Uy) * (1.0 / C2);
   const HermiteA h = hermite_a(v.t, U);
   bool unused = false;  // the range check rules overflow out
-  // omega rho times the Hermite coefficients a_jk (C0 = a00 + a01 q + a02 q^2, ...), each in
-  // the format that keeps its products with the shell constants at 2^-57
-  const long long A00 = fx_from_double(v.R * h.a00, FV, 64, unused);  // |A00| < 4
+  // omega rho times the Hermite coefficients a_jk (C0 = a00 + a01 q + a02 q^2, C1 = a10 +
+  // a11 q, C2 = a20 + a21 q), with the fraction bits that put their products with the
+  // shell constants (cw: 63, cq: 59, cq2: 55) at 57, 59 and 60
+  const long long A00 = fx_from_double(v.R * h.a00, 58, 64, unused);  // |A00| < 4
   const long long A01 = fx_from_double(v.R * h.a01, 62, 64, unused);  // |A01| < 0.6
   const long long A02 = fx_from_double(v.R * h.a02, 66, 64, unused);  // |A02| < 0.03
-  const long long A10 = fx_from_double(v.R * h.a10, FV, 64, unused);  // |A10| < 5
-  const long long A11 = fx_from_double(v.R * h.a11, 62, 64, unused);  // |A11| < 0.4
-  const long long A20 = fx_from_double(v.R * h.a20, FV, 64, unused);  // |A20| < 3
-  const long long A21 = fx_from_double(v.R * h.a21, 62, 64, unused);  // |A21| < 0.2
+  const long long A10 = fx_from_double(v.R * h.a10, 60, 64, unused);  // |A10| < 5
+  const long long A11 = fx_from_double(v.R * h.a11, 64, 64, unused);  // |A11| < 0.4
+  const long long A20 = fx_from_double(v.R * h.a20, 61, 64, unused);  // |A20| < 3
+  const long long A21 = fx_from_double(v.R * h.a21, 65, 64, unused);  // |A21| < 0.2
   const unsigned long long Rf = (unsigned long long)fx_from_double(v.R, 61, 64, unused);  // < 3
-  const long long om1f = fx_from_double(a.cc.om1, FU, 64, unused);
-  const long long X1 = fx_from_double(v.Ux, FU, 64, unused), Y1 = fx_from_double(v.Uy, FU, 64, unused);
+  const long long om1f = fx_from_double(a.cc.om1, 63, 64, unused);                         // |.| < 1
+  const long long X1 = fx_from_double(v.Ux, 63, 64, unused), Y1 = fx_from_double(v.Uy, 63, 64, unused);
   {
     constexpr int e = shell_exp(0);
-    const long long K0 = fx_mulhi(kCw(0), A00) * 2 + 1;
-    store(0, fx_to_double(fx_mulhi(om1f, fx_from_nonneg(sf[0], FV + e)) * 4 + 2 + K0, FV + e));
+    const long long K0 = fx_mulhi_su(A00, kCw(0)) * 2 + 1;
+    store(0, fx_to_double(fx_mulhi_su(om1f, sx[0]) + K0, 58 + e));
   }
-  //   K0 = w' (A00 + q A01 + q^2 A02), K1 = w' (A10 + q A11), K2 = w' (A20 + q A21)  (Q5.58)
-  //   K3 = omega rho w' / 6, K4 = omega rho w' / 24                                   (Q3.61)
+  // K0 (58 bits) = w' (A00 + q A01 + q^2 A02), K1 (59) = w' (A10 + q A11),
+  // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, K4 (62) = omega rho w' / 24,
   // formed at the first pair of each shell (pairs come grouped by shell).
   int cur = -1, e = 0;
   long long K0 = 0, K1 = 0, K2 = 0;
@@ -164,26 +216,26 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     if (sh != cur) {  // uniform across the warp
       cur = sh;
       const ShellFix& c = c_shell_fix[sh];
-      K0 = (fx_mulhi(c.cw, A00) + fx_mulhi(c.cq, A01) + fx_mulhi(c.cq2, A02)) * 2 + 3;
-      K1 = (fx_mulhi(c.cw, A10) + fx_mulhi(c.cq, A11)) * 2 + 2;
-      K2 = (fx_mulhi(c.cw, A20) + fx_mulhi(c.cq, A21)) * 2 + 2;
+      K0 = (fx_mulhi_su(A00, c.cw) + fx_mulhi_su(A01, c.cq) + fx_mulhi_su(A02, c.cq2)) * 2 + 3;
+      K1 = fx_mulhi_su(A10, c.cw) + fx_mulhi_su(A11, c.cq) + 1;
+      K2 = fx_mulhi_su(A20, c.cw) + fx_mulhi_su(A21, c.cq) + 1;
       K3 = fx_umulhi(Rf, c.cw6);
-      K4 = fx_umulhi(Rf, c.cw24);
+      K4 = fx_umulhi(Rf, c.cw24) * 2;
       e = c.e;
     }
     const int vxk = (int)((kPairVx >> (2 * (j - 1))) & 3);
     const int vyk = (int)((kPairVy >> (3 * (j - 1))) & 7) - 3;
-    const long long s = vxk * X1 + vyk * Y1;                                          // Q1.62
+    const long long s = vxk * X1 + vyk * Y1;                                  // 63 bits, |s| < 0.6
     const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
-    const unsigned long long s2 = fx_umulhi(as, as);                                  // Q4.60
-    const long long e1 = K2 + (long long)fx_umulhi(K4, s2) * 2 + 1;                   // Q5.58
-    const long long Ev = K0 + fx_mulhi(e1, (long long)s2) * 16 + 8;                   // 2^-54 -> Q5.58
-    const long long o1 = K1 + (long long)fx_umulhi(K3, s2) * 2 + 1;                   // Q5.58
-    const long long Ov = fx_mulhi(o1, s) * 4 + 2;                                     // 2^-56 -> Q5.58
-    const long long rp = fx_mulhi(om1f, fx_from_nonneg(sf[j * 32], FV + e)) * 4 + 2;
-    const long long rm = fx_mulhi(om1f, fx_from_nonneg(sf[(j + NPAIR) * 32], FV + e)) * 4 + 2;
-    store(j, fx_to_double(rp + Ev + Ov, FV + e));
-    store(j + NPAIR, fx_to_double(rm + Ev - Ov, FV + e));
+    const long long s2 = (long long)fx_umulhi(as, as);                        // 62
+    const long long e1 = K2 + (long long)fx_umulhi(K4, (unsigned long long)s2);  // 60
+    const long long Ev = K0 + fx_mulhi_su(e1, (unsigned long long)s2);        // 58
+    const long long o1 = K1 + (long long)fx_umulhi(K3, (unsigned long long)s2);  // 59
+    const long long Ov = fx_mulhi(o1, s);                                     // 58
+    const long long rp = fx_mulhi_su(om1f, sx[j * 32]);                       // 63 + 59 -> 58
+    const long long rm = fx_mulhi_su(om1f, sx[(j + NPAIR) * 32]);
+    store(j, LBM_FIX64_TO_DOUBLE_PLUS(rp + Ev + Ov + 2, 58 + e));
+    store(j + NPAIR, LBM_FIX64_TO_DOUBLE_MINUS(rm + Ev - Ov + 1, 58 + e));
   }
 }
 

@@ -93,19 +93,22 @@ def test_fixed_and_float64_relaxations_agree_on_a_long_run():
     assert rel_err(to_host(fx, a), to_host(fd, b)) <= 1e-13
 
 
-def test_no_mass_drift_against_float64():
-    """Periodic box without gravity, 400 steps.  The truncations of the fixed-point products
-    are re-centred, so the fixed-point relaxation adds no systematic mass drift: its total
-    mass stays within 1e-14 of the float64 relaxation's (a bias of one unit of 2^-58 per
-    population per step would show as ~1e-15 after 400 steps; an unre-centred truncation of
-    2^-54 as ~2e-14)."""
-    out = []
+def test_no_mass_drift():
+    """Periodic box without gravity, 400 steps: collision conserves mass, so the total may
+    move only by rounding.  The truncations of the fixed-point products are re-centred, so
+    the fixed-point relaxation drifts no more than the float64 one (whose own drift comes
+    from the float64 weights and rounding) and stays within 1e-14 of the initial mass (an
+    unre-centred truncation of 2^-54 per population and step would show as ~1e-14)."""
+    drift = {}
     for prec in (lbm.FP64_FIXED, lbm.FP64):
         p = lbm.Params(64, 64, gy=0.0, bc=lbm.BC_PERIODIC_Y, precision=prec)
         fields = moving_fields(p, 0.05, -0.03, torch.full((p.lx, p.ly), 1.05, dtype=torch.float64))
-        f = lbm.run(p, device_init(p, fields), lbm.empty_state(p), 400)
-        out.append(float(f[:, :, : p.ly].sum()))
-    assert abs(out[0] - out[1]) / out[1] <= 1e-14
+        f0 = device_init(p, fields)
+        m0 = float(f0[:, :, : p.ly].sum())
+        f = lbm.run(p, f0.clone(), lbm.empty_state(p), 400)
+        drift[prec] = abs(float(f[:, :, : p.ly].sum()) - m0) / m0
+    print(f"mass drift after 400 steps: fixed {drift[lbm.FP64_FIXED]:.3g}, float64 {drift[lbm.FP64]:.3g}")
+    assert drift[lbm.FP64_FIXED] <= max(drift[lbm.FP64], 1e-14)
 
 
 def test_state_buffers_interchange_with_fp64():
