@@ -47,18 +47,24 @@ static __constant__ ShellFix c_shell_fix[8] = {LBM_SHELL_FIX(0), LBM_SHELL_FIX(1
                                                LBM_SHELL_FIX(6), LBM_SHELL_FIX(7)};
 #undef LBM_SHELL_FIX
 
+// x >> r with PTX semantics: shift amounts of 64 or more give 0.
+__device__ __forceinline__ unsigned long long shr_clamped(unsigned long long x, unsigned r) {
+  unsigned long long y;
+  asm("shr.b64 %0, %1, %2;" : "=l"(y) : "l"(x), "r"(r));
+  return y;
+}
+
 // round(v 2^k) for a float64 v >= 0 with v 2^k < 2^62 (callers guarantee both); integer
-// instructions only, round half up.  v 2^k = m 2^sh with the 53-bit significand m: the
-// value is formed with one extra fraction bit, m 2^(sh + 1) = (m 2^11) >> (10 - sh), then
-// rounded.  Values below half a unit (shifts past 63) give 0, as do zeros and subnormals.
+// instructions only, round half up.  With the significand m (implicit bit included),
+// v 2^k = m 2^sh; the value is formed with one extra fraction bit,
+// m 2^(sh + 1) = (m 2^11) >> (10 - sh), where m 2^11 is the bit pattern shifted left by 11
+// with the implicit bit set.  Zeros, subnormals and values below half a unit give 0 (their
+// shift is 64 or more).
 __device__ __forceinline__ long long fx_from_nonneg(double v, int k) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int E = (int)(b >> 52);  // sign bit clear
-  unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-  m = E == 0 ? 0ull : m;
-  const int r = 1085 - E - k;  // 10 - sh >= 1 when v 2^k < 2^62
-  const unsigned long long t = r < 64 ? (m << 11) >> r : 0ull;
-  return (long long)((t + 1) >> 1);
+  const unsigned E = (unsigned)(b >> 52);  // sign bit clear
+  const unsigned long long x = (b << 11) | 0x8000000000000000ull;
+  return (long long)((shr_clamped(x, 1085u - E - (unsigned)k) + 1) >> 1);
 }
 
 // 8-byte asynchronous global -> shared copy (sm_80+ LDGSTS), cached in L1.
@@ -75,8 +81,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 #define LBM_FIX64_TO_DOUBLE_MINUS fx_to_double_dp
 #endif
 #ifndef LBM_FIX64_TO_DOUBLE_PLUS
-#define LBM_FIX64_TO_DOUBLE_PLUS fx_to_double
+#define LBM_FIX64_TO_DOUBLE_PLUS fx_to_double_dp
 #endif
+
+template <bool B>
+struct BoolConst {
+  static constexpr bool value = B;
+};
 
 // Shared staging: one warp holds sf[i * 32 + lane] for its 32 sites.
 constexpr int kFixWarps = 4;  // warps per block (block = 32 x 4 threads)
@@ -197,46 +208,54 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   const long long A20 = fx_from_double(v.R * h.a20, 61, 64, unused);  // |A20| < 3
   const long long A21 = fx_from_double(v.R * h.a21, 65, 64, unused);  // |A21| < 0.2
   const unsigned long long Rf = (unsigned long long)fx_from_double(v.R, 61, 64, unused);  // < 3
-  const long long om1f = fx_from_double(a.cc.om1, 63, 64, unused);                         // |.| < 1
+  // |1 - omega| < 1 with 63 fraction bits; its sign is the same for every site, so the
+  // relaxation loop below is instantiated for each sign and multiplies unsigned values
+  const unsigned long long om1u = (unsigned long long)fx_from_double(fabs(a.cc.om1), 63, 64, unused);
   const long long X1 = fx_from_double(v.Ux, 63, 64, unused), Y1 = fx_from_double(v.Uy, 63, 64, unused);
-  {
-    constexpr int e = shell_exp(0);
-    const long long K0 = fx_mulhi_su(A00, kCw(0)) * 2 + 1;
-    store(0, fx_to_double(fx_mulhi_su(om1f, sx[0]) + K0, 58 + e));
-  }
-  // K0 (58 bits) = w' (A00 + q A01 + q^2 A02), K1 (59) = w' (A10 + q A11),
-  // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, K4 (62) = omega rho w' / 24,
-  // formed at the first pair of each shell (pairs come grouped by shell).
-  int cur = -1, e = 0;
-  long long K0 = 0, K1 = 0, K2 = 0;
-  unsigned long long K3 = 0, K4 = 0;
-#pragma unroll 1
-  for (int j = 1; j <= NPAIR; ++j) {
-    const int sh = (int)((kPairShell >> (3 * (j - 1))) & 7);
-    if (sh != cur) {  // uniform across the warp
-      cur = sh;
-      const ShellFix& c = c_shell_fix[sh];
-      K0 = (fx_mulhi_su(A00, c.cw) + fx_mulhi_su(A01, c.cq) + fx_mulhi_su(A02, c.cq2)) * 2 + 3;
-      K1 = fx_mulhi_su(A10, c.cw) + fx_mulhi_su(A11, c.cq) + 1;
-      K2 = fx_mulhi_su(A20, c.cw) + fx_mulhi_su(A21, c.cq) + 1;
-      K3 = fx_umulhi(Rf, c.cw6);
-      K4 = fx_umulhi(Rf, c.cw24) * 2;
-      e = c.e;
+  const auto relax = [&](auto neg) {
+    constexpr bool NEG = decltype(neg)::value;
+    const auto add_r = [](long long v, unsigned long long r) { return NEG ? v - (long long)r : v + (long long)r; };
+    {
+      constexpr int e = shell_exp(0);
+      const long long K0 = fx_mulhi_su(A00, kCw(0)) * 2 + 1;
+      store(0, LBM_FIX64_TO_DOUBLE_PLUS(add_r(K0, fx_umulhi(om1u, sx[0])), 58 + e));
     }
-    const int vxk = (int)((kPairVx >> (2 * (j - 1))) & 3);
-    const int vyk = (int)((kPairVy >> (3 * (j - 1))) & 7) - 3;
-    const long long s = vxk * X1 + vyk * Y1;                                  // 63 bits, |s| < 0.6
-    const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
-    const long long s2 = (long long)fx_umulhi(as, as);                        // 62
-    const long long e1 = K2 + (long long)fx_umulhi(K4, (unsigned long long)s2);  // 60
-    const long long Ev = K0 + fx_mulhi_su(e1, (unsigned long long)s2);        // 58
-    const long long o1 = K1 + (long long)fx_umulhi(K3, (unsigned long long)s2);  // 59
-    const long long Ov = fx_mulhi(o1, s);                                     // 58
-    const long long rp = fx_mulhi_su(om1f, sx[j * 32]);                       // 63 + 59 -> 58
-    const long long rm = fx_mulhi_su(om1f, sx[(j + NPAIR) * 32]);
-    store(j, LBM_FIX64_TO_DOUBLE_PLUS(rp + Ev + Ov + 2, 58 + e));
-    store(j + NPAIR, LBM_FIX64_TO_DOUBLE_MINUS(rm + Ev - Ov + 1, 58 + e));
-  }
+    // K0 (58 bits) = w' (A00 + q A01 + q^2 A02), K1 (59) = w' (A10 + q A11),
+    // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, K4 (62) = omega rho w' / 24,
+    // formed at the first pair of each shell (pairs come grouped by shell).
+    int cur = -1, e = 0;
+    long long K0 = 0, K1 = 0, K2 = 0;
+    unsigned long long K3 = 0, K4 = 0;
+#pragma unroll 1
+    for (int j = 1; j <= NPAIR; ++j) {
+      const int sh = (int)((kPairShell >> (3 * (j - 1))) & 7);
+      if (sh != cur) {  // uniform across the warp
+        cur = sh;
+        const ShellFix& c = c_shell_fix[sh];
+        K0 = (fx_mulhi_su(A00, c.cw) + fx_mulhi_su(A01, c.cq) + fx_mulhi_su(A02, c.cq2)) * 2 + 3;
+        K1 = fx_mulhi_su(A10, c.cw) + fx_mulhi_su(A11, c.cq) + 1;
+        K2 = fx_mulhi_su(A20, c.cw) + fx_mulhi_su(A21, c.cq) + 1;
+        K3 = fx_umulhi(Rf, c.cw6);
+        K4 = fx_umulhi(Rf, c.cw24) * 2;
+        e = c.e;
+      }
+      const int vxk = (int)((kPairVx >> (2 * (j - 1))) & 3);
+      const int vyk = (int)((kPairVy >> (3 * (j - 1))) & 7) - 3;
+      const long long s = vxk * X1 + vyk * Y1;                                  // 63 bits, |s| < 0.6
+      const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
+      const long long s2 = (long long)fx_umulhi(as, as);                        // 62
+      const long long e1 = K2 + (long long)fx_umulhi(K4, (unsigned long long)s2);  // 60
+      const long long Ev = K0 + fx_mulhi_su(e1, (unsigned long long)s2);        // 58
+      const long long o1 = K1 + (long long)fx_umulhi(K3, (unsigned long long)s2);  // 59
+      const long long Ov = fx_mulhi(o1, s);                                     // 58
+      const unsigned long long rp = fx_umulhi(om1u, sx[j * 32]);                // 63 + 59 -> 58
+      const unsigned long long rm = fx_umulhi(om1u, sx[(j + NPAIR) * 32]);
+      store(j, LBM_FIX64_TO_DOUBLE_PLUS(add_r(Ev + Ov + 2, rp), 58 + e));
+      store(j + NPAIR, LBM_FIX64_TO_DOUBLE_MINUS(add_r(Ev - Ov + 1, rm), 58 + e));
+    }
+  };
+  if (a.cc.om1 < 0.0) relax(BoolConst<true>());
+  else relax(BoolConst<false>());
 }
 
 }  // namespace d2q37
