@@ -47,6 +47,14 @@ static __constant__ ShellFix c_shell_fix[8] = {LBM_SHELL_FIX(0), LBM_SHELL_FIX(1
                                                LBM_SHELL_FIX(6), LBM_SHELL_FIX(7)};
 #undef LBM_SHELL_FIX
 
+// round(2^64 / c^2), exact from the float64 c^2 = m 2^x
+__host__ __device__ constexpr unsigned long long inv_c2_64() {
+  const DoubleParts p = double_parts(C2);
+  const unsigned __int128 num = (unsigned __int128)1 << (64 - p.x);
+  return (unsigned long long)((num + p.m / 2) / p.m);
+}
+constexpr unsigned long long kInvC2 = inv_c2_64();
+
 // x >> r with PTX semantics: shift amounts of 64 or more give 0.
 __device__ __forceinline__ unsigned long long shr_clamped(unsigned long long x, unsigned r) {
   unsigned long long y;
@@ -193,25 +201,39 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     collide_site_reloaded<PERIODIC>(fin, fout, a, x, yc, self);
     return;
   }
-  // 4. fixed-point relaxation
-  const double U = fma(v.Ux, v.Ux, v.Uy * v.Uy) * (1.0 / C2);
-  const HermiteA h = hermite_a(v.t, U);
+  // 4. fixed-point relaxation.  Inputs: omega rho, c u_s and t = T_s - 1 from the float64
+  //    stage; everything after them is integer arithmetic.
   bool unused = false;  // the range check rules overflow out
-  // omega rho times the Hermite coefficients a_jk (C0 = a00 + a01 q + a02 q^2, C1 = a10 +
-  // a11 q, C2 = a20 + a21 q), with the fraction bits that put their products with the
-  // shell constants (cw: 63, cq: 59, cq2: 55) at 57, 59 and 60
-  const long long A00 = fx_from_double(v.R * h.a00, 58, 64, unused);  // |A00| < 4
-  const long long A01 = fx_from_double(v.R * h.a01, 62, 64, unused);  // |A01| < 0.6
-  const long long A02 = fx_from_double(v.R * h.a02, 66, 64, unused);  // |A02| < 0.03
-  const long long A10 = fx_from_double(v.R * h.a10, 60, 64, unused);  // |A10| < 5
-  const long long A11 = fx_from_double(v.R * h.a11, 64, 64, unused);  // |A11| < 0.4
-  const long long A20 = fx_from_double(v.R * h.a20, 61, 64, unused);  // |A20| < 3
-  const long long A21 = fx_from_double(v.R * h.a21, 65, 64, unused);  // |A21| < 0.2
   const unsigned long long Rf = (unsigned long long)fx_from_double(v.R, 61, 64, unused);  // < 3
   // |1 - omega| < 1 with 63 fraction bits; its sign is the same for every site, so the
   // relaxation loop below is instantiated for each sign and multiplies unsigned values
   const unsigned long long om1u = (unsigned long long)fx_from_double(fabs(a.cc.om1), 63, 64, unused);
   const long long X1 = fx_from_double(v.Ux, 63, 64, unused), Y1 = fx_from_double(v.Uy, 63, 64, unused);
+  const long long t63 = fx_from_double(v.t, 63, 64, unused);                    // |t| < 0.25
+  // U = |u_s|^2 = (Ux^2 + Uy^2) / c^2 (62 bits), and the products of the Hermite coefficients
+  const unsigned long long ax = (unsigned long long)(X1 < 0 ? -X1 : X1), ay = (unsigned long long)(Y1 < 0 ? -Y1 : Y1);
+  const long long U62 = (long long)fx_umulhi(fx_umulhi(ax, ax) + fx_umulhi(ay, ay), kInvC2);
+  const unsigned long long at = (unsigned long long)(t63 < 0 ? -t63 : t63);
+  const long long tU = fx_mulhi_su(t63, (unsigned long long)U62);              // 61
+  const long long t2 = (long long)fx_umulhi(at, at);                            // 62
+  const long long U2 = (long long)fx_umulhi((unsigned long long)U62, (unsigned long long)U62);  // 60
+  // a_jk of C0 = a00 + a01 q + a02 q^2, C1 = a10 + a11 q, C2 = a20 + a21 q (collide_fp64.cuh),
+  // each with the fraction bits (in brackets) that its size allows:
+  //   a00 = 1 - U/2 - t + U^2/8 + tU + t^2 [61]   a01 = t/2 - tU/4 - t^2 [65]   a02 = t^2/8 [69]
+  //   a10 = 1 - U/2 - 2t [62]   a11 = t/2 [65]   a20 = 1/2 - U/4 - 3t/2 [63]   a21 = t/4 [66]
+  const long long a00 = (1LL << 61) - (U62 >> 2) - (t63 >> 2) + (U2 >> 2) + tU + (t2 >> 1);
+  const long long a01 = t63 * 2 - tU * 4 - t2 * 8;
+  const long long a02 = t2 * 16;
+  const long long a10 = (1LL << 62) - (U62 >> 1) - t63;
+  const long long a11 = t63 * 2;  // also a21, at 66 bits
+  const long long a20 = (1LL << 62) - (U62 >> 1) - t63 - (t63 >> 1);
+  // A = omega rho a (the product with R at 61 bits takes 3 off each)
+  const long long A00 = fx_mulhi_su(a00, Rf);  // 58
+  const long long A01 = fx_mulhi_su(a01, Rf);  // 62
+  const long long A02 = fx_mulhi_su(a02, Rf);  // 66
+  const long long A10 = fx_mulhi_su(a10, Rf);  // 59
+  const long long A11 = fx_mulhi_su(a11, Rf);  // 62 (A21: the same integer at 63)
+  const long long A20 = fx_mulhi_su(a20, Rf);  // 60
   const auto relax = [&](auto neg) {
     constexpr bool NEG = decltype(neg)::value;
     const auto add_r = [](long long v, unsigned long long r) { return NEG ? v - (long long)r : v + (long long)r; };
@@ -233,8 +255,8 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
         cur = sh;
         const ShellFix& c = c_shell_fix[sh];
         K0 = (fx_mulhi_su(A00, c.cw) + fx_mulhi_su(A01, c.cq) + fx_mulhi_su(A02, c.cq2)) * 2 + 3;
-        K1 = fx_mulhi_su(A10, c.cw) + fx_mulhi_su(A11, c.cq) + 1;
-        K2 = fx_mulhi_su(A20, c.cw) + fx_mulhi_su(A21, c.cq) + 1;
+        K1 = fx_mulhi_su(A10, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 58 -> 59, 57 -> 59
+        K2 = fx_mulhi_su(A20, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 59 -> 60, 58 -> 60
         K3 = fx_umulhi(Rf, c.cw6);
         K4 = fx_umulhi(Rf, c.cw24) * 2;
         e = c.e;
