@@ -41,7 +41,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture
 # of the current kernel on a smaller lattice, scaled to 4096 x 8192 by the site count;
 # profiles/ holds the captures).  None where no capture of the current kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = {"fused": 18.13e9, "separate": None, "fp32": 9.16e9}
+TRAFFIC_BYTES_PER_LAUNCH = {"fused": 18.13e9, "separate": None, "fp32": 9.16e9, "fp64fix": 19.09e9}
 
 
 def _hbm_peak():
@@ -69,6 +69,8 @@ def _args():
                     help="fp32 = FP32 shifted-deviation storage (fused only); fp64fix = float64 storage "
                          "with the fixed-point relaxation (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fixed", action="store_true",
+                    help="skip the extra timing of the fixed-point-relaxation FP64 step")
     ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
                     help="batch = 256 independent lattices of uneven sizes; adjoint = gradient of the "
                          "kinetic energy after 500 steps of a 512x1024 lattice (checkpoints every 22)")
@@ -281,6 +283,34 @@ def run_ours(a):
                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                     "hbm_gbs_equiv": BYTES_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e9}
 
+    # the same FP64 step with the fixed-point relaxation (LBM_FP64_FIXED), on the same lattice
+    fixed_line = None
+    if a.precision == "fp64" and a.variant == "fused" and not a.no_fixed:
+        pf = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP, precision=lbm.FP64_FIXED)
+        lbm.init(pf, *dev, bufs[0])
+        for k in range(a.warmup):
+            lbm.step(pf, bufs[k % 2], bufs[(k + 1) % 2], stream)
+        torch.cuda.synchronize()
+        fev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with ClockSampler(local) as fclk:
+            fev[0].record(stream)
+            for k in range(a.steps):
+                lbm.step(pf, bufs[(a.warmup + k) % 2], bufs[(a.warmup + k + 1) % 2], stream)
+            fev[1].record(stream)
+            torch.cuda.synchronize()
+        f_ms = max_over_ranks(fev[0].elapsed_time(fev[1]), "cuda")
+        f_kern = f_ms / a.steps
+        f_gbs = BYTES_PER_SITE_FP64 * sites / (f_kern * 1e-3) / 1e9
+        fixed_line = {"value": whole_job_mlups(sites, a.steps, world, f_ms), "unit": "MLUPS",
+                      "ms_per_step": f_kern, "dtype": "f64+i64", "kernel": "k_step_fix64",
+                      "what": "float64 states; equilibrium and relaxation in 64-bit fixed point on the "
+                              "integer pipes (float64 outside its range); same parity bars as FP64",
+                      "roofline": {"bound": "hbm", "achieved": f_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                   "frac": f_gbs / HBM_PEAK_GBS,
+                                   "traffic": TRAFFIC_BYTES_PER_LAUNCH.get("fp64fix"),
+                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                      "gpu_launches": a.steps, "clocks": fclk.summary()}
+
     # the propagate kernel alone (Table "propagate-kernel" of Sec. 4): a pure copy of every
     # population whose source is inside the fluid, timed over the same number of launches
     prop_line = None
@@ -331,6 +361,7 @@ def run_ours(a):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e,
                 **({"propagate_kernel": prop_line} if prop_line else {}),
+                **({"fp64_fixed_relax": fixed_line} if fixed_line else {}),
                 "gpu_launches": a.steps * (3 if separate else 1),
                 "clocks": clk.summary()}
         if not a.no_cpu_baseline and world == 1 and (lx, ly) == (LX, LY):
@@ -352,7 +383,8 @@ def run_batch(a):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     fp32 = a.precision == "fp32"
-    prec = lbm.FP32_SHIFTED if fp32 else lbm.FP64
+    fix = a.precision == "fp64fix"
+    prec = lbm.FP32_SHIFTED if fp32 else (lbm.FP64_FIXED if fix else lbm.FP64)
     spec = I.batch_workload(seed=4 + rank, n=a.batch_n)
     params, fa, fb = [], [], []
     for lx, ly, tau, s in spec:
@@ -389,12 +421,13 @@ def run_batch(a):
     ms_loop = timed((lbm.BATCH_LOOP, 4, 0), a.steps)
     value = sites * a.steps / (ms * 1e-3) / 1e6
     bytes_site = BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64
-    if fp32:
+    kind = "fp32" if fp32 else ("fix64" if fix else "fp64")
+    if fp32 or fix:
         achieved = bytes_site * sites * a.steps / (ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_PEAK_GBS, "traffic": None,
-                    "kernel": ("k_batch_persistent<float>" if cfg["mode"] == lbm.BATCH_PERSISTENT
-                               else "k_batch_step<float>")}
+                    "kernel": ("k_batch_persistent<" if cfg["mode"] == lbm.BATCH_PERSISTENT
+                               else "k_batch_step<") + kind + ">"}
     else:
         achieved = FLOPS_PER_SITE_FP64 * sites * a.steps / (ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -404,7 +437,8 @@ def run_batch(a):
     if rank == 0:
         line = {"metric": "D2Q37 MLUPS (batched)", "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64" if fp32 else "f64",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+i64+f64" if fp32 else ("f64+i64" if fix else "f64"),
                 "data": "synthetic",
                 "config": {"workload": f"{len(spec)} RT lattices, Lx in 128..1024, Ly = 2 Lx, tau in [0.6, 1.0]",
                            "sites": sites, "precision": a.precision, "autotuned": cfg,

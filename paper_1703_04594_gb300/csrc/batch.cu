@@ -6,7 +6,8 @@
 // fastest inside a lattice) and a device table gives each tile's lattice, so everything a
 // block reads about its lattice is uniform across the block.  Each warp runs the same strip
 // step as the single-lattice kernels (step_fp64.cuh / step_fp32.cuh), so results are
-// bit-identical to lbm_run per lattice.
+// bit-identical to lbm_run per lattice (all three forms: FP64, FP64 with the fixed-point
+// relaxation, whose blocks stage their strips in dynamic shared memory, and FP32).
 //
 // Modes:
 //   LBM_BATCH_PER_STEP   one launch per step over all tiles of all lattices;
@@ -30,6 +31,7 @@
 
 #include "../../include/lbm_d2q37.h"
 #include "kernels.h"
+#include "step_fix64.cuh"
 #include "step_fp32.cuh"
 
 namespace d2q37 {
@@ -51,12 +53,30 @@ struct BatchSync {
 
 namespace {
 
-// Tile t of the batch (32 rows x 4 columns, one warp per column, as the single-lattice
+// Step kinds: the strip functions of the three storage/arithmetic forms.
+enum BatchKind { kFp64 = 0, kFp32 = 1, kFix64 = 2 };
+
+template <int K>
+struct KindOf {
+  using T = double;
+};
+template <>
+struct KindOf<kFp32> {
+  using T = float;
+};
+
+// Shared memory of a block: the fixed-point form stages 37 x 32 doubles per warp.
+inline size_t batch_smem_bytes(int kind, int warps) {
+  return kind == kFix64 ? (size_t)warps * Q * 32 * sizeof(double) : 0;
+}
+
+// Tile t of the batch (32 rows x TX columns, one warp per column, as the single-lattice
 // kernels): its lattice comes from a per-tile table, so everything that depends on the
 // lattice is uniform across the block.
-template <class T, bool PERIODIC, class Ld>
+template <int KIND, bool PERIODIC, class Ld>
 __device__ __forceinline__ void batch_tile(const BatchLattice* __restrict__ L, const unsigned short* __restrict__ tl,
-                                           long long t, int parity, Ld ld) {
+                                           long long t, int parity, Ld ld, double* staged) {
+  using T = typename KindOf<KIND>::T;
   const int j = tl[t];
   const BatchLattice& B = L[j];
   const long long local = t - B.tile_begin;
@@ -66,7 +86,9 @@ __device__ __forceinline__ void batch_tile(const BatchLattice* __restrict__ L, c
   if (x >= B.a.lx) return;  // uniform per warp
   const T* src = (const T*)B.f[parity];
   T* dst = (T*)B.f[parity ^ 1];
-  if constexpr (sizeof(T) == 8) step_strip_fp64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
+  if constexpr (KIND == kFp64) step_strip_fp64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
+  else if constexpr (KIND == kFix64)
+    step_strip_fix64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld, staged + threadIdx.y * (Q * 32));
   else step_strip_fp32<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
 }
 
@@ -114,25 +136,32 @@ __device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, l
 
 }  // namespace
 
-// Register cap: at most 256 threads per block (8 warps); the FP32 step keeps two such
-// blocks resident per SM (<= 128 registers), as the single-lattice FP32 kernel does.
-template <class T, bool PERIODIC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_batch_step(const BatchLattice* __restrict__ L,
+// Register caps: at most 256 threads per block (8 warps).  The FP32 step keeps three such
+// blocks resident per SM (<= 85 registers), the fixed-point FP64 step likewise (its shared
+// staging allows 6 blocks of 4 warps), the float64 step two (128 registers, as its
+// single-lattice kernel).
+constexpr int batch_min_blocks(int kind) { return kind == kFp64 ? 2 : 3; }
+
+extern __shared__ double batch_staged[];
+
+template <int KIND, bool PERIODIC>
+__global__ void __launch_bounds__(256, batch_min_blocks(KIND)) k_batch_step(const BatchLattice* __restrict__ L,
                                                     const unsigned short* __restrict__ tl, long long total,
                                                     int parity) {
   const long long t = blockIdx.x;
   if (t >= total) return;
-  batch_tile<T, PERIODIC>(L, tl, t, parity, LdReadOnly());
+  batch_tile<KIND, PERIODIC>(L, tl, t, parity, LdReadOnly(), batch_staged);
 }
 
-template <class T, bool PERIODIC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_batch_persistent(const BatchLattice* __restrict__ L,
+template <int KIND, bool PERIODIC>
+__global__ void __launch_bounds__(256, batch_min_blocks(KIND)) k_batch_persistent(const BatchLattice* __restrict__ L,
                                                           const unsigned short* __restrict__ tl, long long total,
                                                           int parity0, int steps, BatchSync* sync, unsigned phantom,
                                                           long long timeout_ns) {
   for (int st = 0; st < steps; ++st) {
     const int parity = (parity0 + st) & 1;
-    for (long long t = blockIdx.x; t < total; t += gridDim.x) batch_tile<T, PERIODIC>(L, tl, t, parity, LdL2());
+    for (long long t = blockIdx.x; t < total; t += gridDim.x)
+      batch_tile<KIND, PERIODIC>(L, tl, t, parity, LdL2(), batch_staged);
     if (st + 1 < steps && !grid_barrier(sync, (unsigned)(st + 1) * gridDim.x + phantom, timeout_ns, st)) return;
   }
 }
@@ -171,41 +200,67 @@ int32_t cuda_status(cudaError_t e) {
   return LBM_ECUDA;
 }
 
-template <class T, bool P>
-void* persistent_fn() {
-  return (void*)k_batch_persistent<T, P>;
+int kind_of(const lbm_batch* b) {
+  return b->precision == LBM_FP64_FIXED ? kFix64 : (b->precision == LBM_FP32_SHIFTED ? kFp32 : kFp64);
+}
+
+template <int K>
+void* persistent_fn(bool periodic) {
+  return periodic ? (void*)k_batch_persistent<K, true> : (void*)k_batch_persistent<K, false>;
+}
+template <int K>
+void* per_step_fn(bool periodic) {
+  return periodic ? (void*)k_batch_step<K, true> : (void*)k_batch_step<K, false>;
 }
 
 void* persistent_kernel(const lbm_batch* b) {
-  if (b->precision == LBM_FP64) return b->periodic ? persistent_fn<double, true>() : persistent_fn<double, false>();
-  return b->periodic ? persistent_fn<float, true>() : persistent_fn<float, false>();
+  switch (kind_of(b)) {
+    case kFix64: return persistent_fn<kFix64>(b->periodic);
+    case kFp32: return persistent_fn<kFp32>(b->periodic);
+    default: return persistent_fn<kFp64>(b->periodic);
+  }
+}
+void* per_step_kernel(const lbm_batch* b) {
+  switch (kind_of(b)) {
+    case kFix64: return per_step_fn<kFix64>(b->periodic);
+    case kFp32: return per_step_fn<kFp32>(b->periodic);
+    default: return per_step_fn<kFp64>(b->periodic);
+  }
 }
 
+// Raises both kernels' dynamic shared memory limit to the largest staging a block can
+// need (8 warps); called once per plan.
+int32_t allow_batch_smem(const lbm_batch* b) {
+  const size_t smem = batch_smem_bytes(kind_of(b), 8);
+  if (smem <= 48 * 1024) return LBM_OK;
+  if (cudaFuncSetAttribute(persistent_kernel(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(per_step_kernel(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return cuda_status(cudaGetLastError());
+  return LBM_OK;
+}
+
+// Blocks of wpb warps that fit on one SM for the persistent kernel.
 int max_blocks_per_sm(const lbm_batch* b, int wpb) {
+  const size_t smem = batch_smem_bytes(kind_of(b), wpb);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel(b), 32 * wpb, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel(b), 32 * wpb, smem) != cudaSuccess)
+    return 0;
   return nb;
-}
-
-template <class T, bool P>
-void launch_step_kernel(const lbm_batch* b, int par, cudaStream_t s) {
-  const dim3 blk(32, b->warps_per_block);
-  k_batch_step<T, P><<<(unsigned)b->total_tiles, blk, 0, s>>>(b->dev_lattices, b->dev_tile_lattice, b->total_tiles,
-                                                              par);
 }
 
 int32_t launch_per_step(lbm_batch* b, int steps, cudaStream_t s) {
   if (b->total_tiles > 0x7fffffffLL) return LBM_EINVAL;
+  const size_t smem = batch_smem_bytes(kind_of(b), b->warps_per_block);
+  const BatchLattice* L = b->dev_lattices;
+  const unsigned short* tl = b->dev_tile_lattice;
+  long long total = b->total_tiles;
   for (int st = 0; st < steps; ++st) {
-    const int par = (b->parity + st) & 1;
-    if (b->precision == LBM_FP64) {
-      if (b->periodic) launch_step_kernel<double, true>(b, par, s);
-      else launch_step_kernel<double, false>(b, par, s);
-    } else {
-      if (b->periodic) launch_step_kernel<float, true>(b, par, s);
-      else launch_step_kernel<float, false>(b, par, s);
-    }
-    const int32_t st_ = cuda_status(cudaGetLastError());
+    int par = (b->parity + st) & 1;
+    void* args[] = {(void*)&L, (void*)&tl, &total, &par};
+    const int32_t st_ = cuda_status(cudaLaunchKernel(per_step_kernel(b), dim3((unsigned)total),
+                                                     dim3(32, b->warps_per_block), args, smem, s));
     if (st_ != LBM_OK) return st_;
   }
   return LBM_OK;
@@ -231,7 +286,7 @@ int32_t launch_persistent(lbm_batch* b, int steps, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(32, wpb);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = batch_smem_bytes(kind_of(b), wpb);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -308,7 +363,6 @@ extern "C" {
 
 int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* f_b, int32_t n, lbm_batch** out) {
   if (!params || !f_a || !f_b || !out || n <= 0 || n > 65535) return LBM_EINVAL;
-  if (params[0].precision != LBM_FP64 && params[0].precision != LBM_FP32_SHIFTED) return LBM_EINVAL;
   *out = nullptr;
   lbm_batch* b = new lbm_batch();
   b->n = n;
@@ -344,7 +398,8 @@ int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* 
     delete b;
     return LBM_ENOMEM;
   }
-  if (relayout(b, 4) != LBM_OK || cudaMemset(b->dev_sync, 0, sizeof(BatchSync)) != cudaSuccess) {
+  if (relayout(b, 4) != LBM_OK || cudaMemset(b->dev_sync, 0, sizeof(BatchSync)) != cudaSuccess ||
+      allow_batch_smem(b) != LBM_OK) {
     cudaFree(b->dev_tile_lattice);
     cudaFree(b->dev_lattices);
     cudaFree(b->dev_sync);

@@ -2,7 +2,8 @@
 //
 // Layout of the work, chosen for the integer pipes:
 //   1. the 37 pull-gathered populations of the strip are copied global -> shared memory
-//      with cp.async (no registers held while the loads are in flight);
+//      with cp.async (no registers held while the loads are in flight; inside a persistent
+//      kernel, whose sources were written earlier in the same launch, with L2 loads);
 //   2. moments: a rolled loop over opposite pairs reads shared memory and sums in 64-bit
 //      fixed point (collide_fp64.cuh), checking the range of the fixed-point path;
 //   3. site scalars in float64 (1/rho, u, T, gravity shift, Hermite coefficients);
@@ -111,20 +112,21 @@ __device__ __forceinline__ const double* gather_src(const double* fin, const Ste
 // The float64 collision of one interior site on values loaded again from global memory:
 // the path of sites outside the fixed-point range.  Not inlined, so that its 37 live
 // float64 values do not weigh on the register allocation of the fixed-point path.
-template <bool PERIODIC>
+template <bool PERIODIC, class Ld>
 __device__ __noinline__ void collide_site_reloaded(const double* __restrict__ fin, double* __restrict__ fout,
                                                    const StepScalars& a, int x, int yc, unsigned self) {
+  const Ld ld;
   double f[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = __ldg(gather_src<PERIODIC>(fin, a, x, yc, i));
+  for (int i = 0; i < Q; ++i) f[i] = ld(gather_src<PERIODIC>(fin, a, x, yc, i));
   collide_site(f, a.cc, [&](int i, double val) { __stcs(fout + i * a.pop + self, val); });
 }
 
 // The float64 strip of a warp next to a wall, not inlined for the same reason.
-template <bool PERIODIC>
+template <bool PERIODIC, class Ld>
 __device__ __noinline__ void wall_strip_fp64(const double* __restrict__ fin, double* __restrict__ fout,
                                              const StepScalars& a, const StepWalls& w, int x, int y0) {
-  step_strip_fp64<PERIODIC>(fin, fout, a, w, x, y0, LdReadOnly());
+  step_strip_fp64<PERIODIC>(fin, fout, a, w, x, y0, Ld());
 }
 
 template <bool PERIODIC, class Ld>
@@ -133,7 +135,7 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
                                                  double* __restrict__ sf) {
   const bool wall_warp = !PERIODIC && (y0 < 3 || y0 + 32 > a.ly - 3);
   if (wall_warp) {
-    wall_strip_fp64<PERIODIC>(fin, fout, a, w, x, y0);
+    wall_strip_fp64<PERIODIC, Ld>(fin, fout, a, w, x, y0);
     return;
   }
   const int lane = threadIdx.x & 31;
@@ -149,9 +151,10 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     for (int i = 0; i < Q; ++i) {
       const double* src = PERIODIC ? fin + i * a.pop + (off[vx(i) + 3] - yc) + wrap_index(yc - vy(i), a.ly)
                                    : fin + i * a.pop + (off[vx(i) + 3] - vy(i));
-      cp_async8(sf + i * 32 + lane, src);
+      if (Ld::kL1) cp_async8(sf + i * 32 + lane, src);
+      else sf[i * 32 + lane] = ld(src);
     }
-    cp_async_wait_all();
+    if (Ld::kL1) cp_async_wait_all();
     __syncwarp();
   }
   sf += lane;
@@ -160,7 +163,6 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   //    moments from f' rounded to 2^-56: rho, j and sum |v|^2 f stay below 2^4 there for
   //    every state in range.  The exponent field of a population in range is at most
   //    1025 - e_s; a negative one has the sign bit set, so one unsigned compare flags both.
-  constexpr double S = 1.0 / 72057594037927936.0;  // 2^-56
   bool out;
   long long R, Ei = 0, Jx = 0, Jy = 0;
   {
@@ -196,9 +198,10 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   const auto store = [&](int i, double val) { __stcs(fout + i * a.pop + self, val); };
   // 3. site scalars in float64; sites out of range (negative or large populations, fast or
   //    hot fluid) take the float64 collision
-  const SiteScalars v = scalars_from_moments((double)R * S, (double)Jx * S, (double)Jy * S, (double)Ei * S, a.cc);
+  const SiteScalars v = scalars_from_moments(fx_to_double_dp(R, 56), fx_to_double_dp(Jx, 56),
+                                             fx_to_double_dp(Jy, 56), fx_to_double_dp(Ei, 56), a.cc);
   if (out || !fixed_range_ok(v)) {
-    collide_site_reloaded<PERIODIC>(fin, fout, a, x, yc, self);
+    collide_site_reloaded<PERIODIC, Ld>(fin, fout, a, x, yc, self);
     return;
   }
   // 4. fixed-point relaxation.  Inputs: omega rho, c u_s and t = T_s - 1 from the float64

@@ -9,11 +9,15 @@
 
 namespace d2q37 {
 
+// kL1: the loads may be served from L1 (sources written by earlier launches only), which
+// also allows staging through L1-cached asynchronous copies.
 struct LdReadOnly {
+  static constexpr bool kL1 = true;
   template <class T>
   __device__ __forceinline__ T operator()(const T* p) const { return __ldg(p); }
 };
 struct LdL2 {
+  static constexpr bool kL1 = false;
   template <class T>
   __device__ __forceinline__ T operator()(const T* p) const { return __ldcg(p); }
 };

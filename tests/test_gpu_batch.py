@@ -1,7 +1,8 @@
 """Batched stepping of independent lattices of uneven sizes (C-ABI lbm_batch_*).
 
 Every mode runs the same per-strip step as the single-lattice kernel, so each lattice of a
-batch must equal lbm_run on that lattice bit for bit (FP64 and FP32 storage).  The
+batch must equal lbm_run on that lattice bit for bit (FP64, FP64 with the fixed-point
+relaxation, and FP32 storage).  The
 persistent mode's grid barrier is bounded in time: a test makes the wait expire (a
 barrier that waits for a block that never arrives) and checks the reported status and
 that the GPU context stays usable.
@@ -48,7 +49,7 @@ def assert_equal_states(params, got, want):
         assert torch.equal(g[:, :, : p.ly], w[:, :, : p.ly]), p
 
 
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_SHIFTED])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_SHIFTED, lbm.FP64_FIXED])
 @pytest.mark.parametrize("mode,tx", [(lbm.BATCH_PER_STEP, 4), (lbm.BATCH_PER_STEP, 1), (lbm.BATCH_PER_STEP, 8),
                                       (lbm.BATCH_PERSISTENT, 4), (lbm.BATCH_PERSISTENT, 2), (lbm.BATCH_LOOP, 4)])
 def test_batch_equals_single_lattice_runs(precision, mode, tx):
