@@ -11,7 +11,7 @@
 //      the equilibrium polynomial and (1 - omega) f + omega f^eq in fixed point.
 // Rolled loops keep the kernel's code small: the fully unrolled form of this arithmetic is
 // ~8000 instructions per site, which thrashes the instruction cache.  Per-pair velocities
-// and shells come from packed immediates, per-shell constants from a constant-memory table.
+// and shells, and per-shell constants, come from constant-memory tables.
 // Sites outside the fixed-point range take the float64 relaxation on the same staged values.
 // Warps next to a wall (two strips per column) run the float64 strip of step_fp64.cuh.
 #pragma once
@@ -20,20 +20,19 @@
 
 namespace d2q37 {
 
-// Representatives 1..18 packed into 64-bit immediates: vx in 2 bits, vy + 3 and the shell in
-// 3 bits each, pair j at bit (j - 1) times the width.
-__host__ __device__ constexpr unsigned long long pack_pairs(int field) {
-  unsigned long long r = 0;
-  for (int j = 1; j <= NPAIR; ++j) {
-    if (field == 0) r |= (unsigned long long)rep_vx(j) << (2 * (j - 1));
-    if (field == 1) r |= (unsigned long long)(rep_vy(j) + 3) << (3 * (j - 1));
-    if (field == 2) r |= (unsigned long long)shell(j) << (3 * (j - 1));
-  }
-  return r;
-}
-constexpr unsigned long long kPairVx = pack_pairs(0);
-constexpr unsigned long long kPairVy = pack_pairs(1);
-constexpr unsigned long long kPairShell = pack_pairs(2);
+// Per-pair data of representatives 1..18 as a constant-memory table (one uniform load per
+// pair; cheaper in issue slots than unpacking the values from immediates).
+struct PairFix {
+  int vx, vy, v2, sh;
+};
+#define LBM_PAIR_FIX(j) \
+  { rep_vx(j), rep_vy(j), rep_vx(j) * rep_vx(j) + rep_vy(j) * rep_vy(j), shell(j) }
+static __constant__ PairFix c_pair_fix[NPAIR + 1] = {
+    LBM_PAIR_FIX(0),  LBM_PAIR_FIX(1),  LBM_PAIR_FIX(2),  LBM_PAIR_FIX(3),  LBM_PAIR_FIX(4),
+    LBM_PAIR_FIX(5),  LBM_PAIR_FIX(6),  LBM_PAIR_FIX(7),  LBM_PAIR_FIX(8),  LBM_PAIR_FIX(9),
+    LBM_PAIR_FIX(10), LBM_PAIR_FIX(11), LBM_PAIR_FIX(12), LBM_PAIR_FIX(13), LBM_PAIR_FIX(14),
+    LBM_PAIR_FIX(15), LBM_PAIR_FIX(16), LBM_PAIR_FIX(17), LBM_PAIR_FIX(18)};
+#undef LBM_PAIR_FIX
 
 struct ShellFix {
   long long cw, cq, cq2;
@@ -175,9 +174,9 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   }
 #pragma unroll 1
   for (int k = 1; k <= NPAIR; ++k) {
-    const int vxk = (int)((kPairVx >> (2 * (k - 1))) & 3);
-    const int vyk = (int)((kPairVy >> (3 * (k - 1))) & 7) - 3;
-    const ShellFix& c = c_shell_fix[(kPairShell >> (3 * (k - 1))) & 7];
+    const PairFix pk = c_pair_fix[k];
+    const int vxk = pk.vx, vyk = pk.vy;
+    const ShellFix& c = c_shell_fix[pk.sh];
     const double fa = sf[k * 32], fb = sf[(k + NPAIR) * 32];
     out |= ((unsigned long long)__double_as_longlong(fa) >> 52 > (unsigned)c.lim) |
            ((unsigned long long)__double_as_longlong(fb) >> 52 > (unsigned)c.lim);
@@ -189,7 +188,7 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     const long long va = (qa + half) >> sh, vb = (qb + half) >> sh;
     const long long P = va + vb, M = va - vb;
     R += P;
-    Ei += (long long)(vxk * vxk + vyk * vyk) * P;
+    Ei += (long long)pk.v2 * P;
     Jx += (long long)vxk * M;
     Jy += (long long)vyk * M;
   }
@@ -253,7 +252,8 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     unsigned long long K3 = 0, K4 = 0;
 #pragma unroll 1
     for (int j = 1; j <= NPAIR; ++j) {
-      const int sh = (int)((kPairShell >> (3 * (j - 1))) & 7);
+      const PairFix pj = c_pair_fix[j];
+      const int sh = pj.sh;
       if (sh != cur) {  // uniform across the warp
         cur = sh;
         const ShellFix& c = c_shell_fix[sh];
@@ -264,8 +264,7 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
         K4 = fx_umulhi(Rf, c.cw24) * 2;
         e = c.e;
       }
-      const int vxk = (int)((kPairVx >> (2 * (j - 1))) & 3);
-      const int vyk = (int)((kPairVy >> (3 * (j - 1))) & 7) - 3;
+      const int vxk = pj.vx, vyk = pj.vy;
       const long long s = vxk * X1 + vyk * Y1;                                  // 63 bits, |s| < 0.6
       const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
       const long long s2 = (long long)fx_umulhi(as, as);                        // 62

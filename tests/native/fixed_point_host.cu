@@ -1,0 +1,58 @@
+// Host build of the fixed-point helpers of the FP64 fixed-point relaxation, for the CPU
+// tests: reads commands from stdin and prints results, one per line.
+//   from <v as hex bits> <k>        -> fx_from_double(v, k) (decimal)
+//   to <X decimal> <k>              -> fx_to_double(X, k) (hex bits)
+//   mulsu <a decimal> <b decimal>   -> fx_mulhi_su(a, b)
+//   mul <a decimal> <b decimal>     -> fx_mulhi(a, b)
+//   umul <a decimal> <b decimal>    -> fx_umulhi(a, b)
+//   const                           -> the shell constants, one shell per line
+#include <cstdio>
+#include <cstring>
+#include <cstdlib>
+
+#include "../../paper_1703_04594_gb300/csrc/collide_fix64.cuh"
+
+using namespace d2q37;
+
+int main() {
+  char cmd[16];
+  while (std::scanf("%15s", cmd) == 1) {
+    if (!std::strcmp(cmd, "from")) {
+      unsigned long long bits;
+      int k;
+      std::scanf("%llx %d", &bits, &k);
+      double v;
+      std::memcpy(&v, &bits, 8);
+      bool ovf = false;
+      const long long r = fx_from_double(v, k, 64, ovf);
+      std::printf("%lld\n", r);
+    } else if (!std::strcmp(cmd, "to")) {
+      long long X;
+      int k;
+      std::scanf("%lld %d", &X, &k);
+      const double d = fx_to_double(X, k);
+      unsigned long long bits;
+      std::memcpy(&bits, &d, 8);
+      std::printf("%016llx\n", bits);
+    } else if (!std::strcmp(cmd, "mulsu")) {
+      long long a;
+      unsigned long long b;
+      std::scanf("%lld %llu", &a, &b);
+      std::printf("%lld\n", fx_mulhi_su(a, b));
+    } else if (!std::strcmp(cmd, "mul")) {
+      long long a, b;
+      std::scanf("%lld %lld", &a, &b);
+      std::printf("%lld\n", fx_mulhi(a, b));
+    } else if (!std::strcmp(cmd, "umul")) {
+      unsigned long long a, b;
+      std::scanf("%llu %llu", &a, &b);
+      std::printf("%llu\n", fx_umulhi(a, b));
+    } else if (!std::strcmp(cmd, "const")) {
+      for (int s = 0; s < 8; ++s)
+        std::printf("%d %d %lld %lld %lld %llu %llu\n", s, shell_exp(s), kCw(s), kCq(s), kCq2(s), kCw6(s), kCw24(s));
+    } else {
+      return 2;
+    }
+  }
+  return 0;
+}

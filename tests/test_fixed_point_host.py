@@ -1,0 +1,126 @@
+"""Host build of the fixed-point helpers behind LBM_FP64_FIXED, against exact arithmetic.
+
+The kernel's 64-bit fixed-point conversions, products and compile-time shell constants are
+`__host__ __device__`; `tests/native/fixed_point_host.cu` compiles them for the CPU and
+this test checks them with Python's exact integers and fractions: conversions round to
+nearest (ties away from zero in magnitude), products keep the floor of the high 64 bits,
+and every shell constant is the correctly rounded value of its definition from the
+library's own float64 weights and lattice scale.
+"""
+import os
+import random
+import shutil
+import struct
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+from paper_1703_04594_gb300 import lbm
+from tests.gpu_util import ensure_built
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "native", "fixed_point_host.cu")
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    assert os.path.exists(nvcc), "nvcc is required to build the host probe"
+    exe = str(tmp_path_factory.mktemp("fx") / "fixed_point_host")
+    subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-o", exe, SRC], check=True,
+                   capture_output=True)
+
+    def run(lines):
+        out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+        return out.stdout.split("\n")[:-1]
+    return run
+
+
+def bits(v: float) -> str:
+    return format(struct.unpack("<Q", struct.pack("<d", v))[0], "x")
+
+
+def from_bits(h: str) -> float:
+    return struct.unpack("<d", struct.pack("<Q", int(h, 16)))[0]
+
+
+def round_half_away(q: Fraction) -> int:
+    n = abs(q)
+    r = int(n) + (1 if n - int(n) >= Fraction(1, 2) else 0)
+    return r if q >= 0 else -r
+
+
+def test_shell_constants_are_exact(probe):
+    ensure_built()
+    c, w, vx, vy = lbm.model()
+    c2 = c * c                                      # the float64 product the kernel uses
+    shells = sorted({vx[i] ** 2 + vy[i] ** 2 for i in range(37)})
+    w_of = {vx[i] ** 2 + vy[i] ** 2: w[i] for i in range(37)}
+    rows = [list(map(int, line.split())) for line in probe(["const"])]
+    for s, e, cw, cq, cq2, cw6, cw24 in rows:
+        v2 = shells[s]
+        ws = Fraction(w_of[v2])
+        assert Fraction(1, 2) <= ws * 2 ** e < 1                   # w_s 2^e_s in [0.5, 1)
+        assert cw == round_half_away(ws * 2 ** (e + 63))
+        assert cw6 == round_half_away(ws * 2 ** (e + 64) / 6)
+        assert cw24 == round_half_away(ws * 2 ** (e + 64) / 24)
+        if s == 0:
+            continue
+        q = Fraction(c2 * v2)                                      # float64 q_s = c^2 |v|^2
+        assert cq == round_half_away(ws * q * 2 ** (e + 59))
+        assert abs(cq2 - ws * q * q * 2 ** (e + 55)) <= 1          # one intermediate rounding
+
+
+def test_double_to_fixed_rounds_to_nearest(probe):
+    rng = random.Random(7)
+    cases = [(0.0, 60), (-0.0, 60), (1.0, 62), (0.2, 60), (-0.2, 60), (7.999999, 58), (2.0 ** -40, 58),
+             (3.0 * 2.0 ** -61, 60), (2.5 * 2.0 ** -60, 60), (-2.5 * 2.0 ** -60, 60), (5e-324, 62)]
+    for _ in range(400):
+        k = rng.randint(56, 69)
+        mag = 2.0 ** rng.uniform(-30, 3 + 58 - k)                  # |v| 2^k < 2^62
+        cases.append((rng.choice([-1, 1]) * mag, k))
+    out = probe([f"from {bits(v)} {k}" for v, k in cases])
+    for (v, k), got in zip(cases, out):
+        assert int(got) == round_half_away(Fraction(v) * 2 ** k), (v, k)
+
+
+def to_double_half_away(X: int, k: int) -> float:
+    """X 2^-k rounded to 53 significant bits, ties away from zero in magnitude."""
+    if X == 0:
+        return 0.0
+    q = Fraction(abs(X), 2 ** k)
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    if Fraction(2) ** e > q:
+        e -= 1
+    m = round_half_away(q / Fraction(2) ** (e - 52))               # 53-bit significand
+    v = float(Fraction(m) * Fraction(2) ** (e - 52))
+    return v if X > 0 else -v
+
+
+def test_fixed_to_double_rounds_to_nearest(probe):
+    rng = random.Random(8)
+    cases = [(1, 58), (-1, 58), (2 ** 62, 60), ((1 << 62) - 1, 60), (-(1 << 62) + 1, 62), ((1 << 53) + 1, 58),
+             ((1 << 54) + 2, 58), (((1 << 53) - 1) << 10 | (1 << 9), 64)]    # a tie that carries
+    for _ in range(400):
+        X = rng.randint(1, (1 << rng.randint(1, 62)) - 1) * rng.choice([-1, 1])
+        cases.append((X, rng.randint(56, 70)))
+    out = probe([f"to {X} {k}" for X, k in cases])
+    for (X, k), got in zip(cases, out):
+        assert from_bits(got) == to_double_half_away(X, k), (X, k)
+
+
+def test_products_keep_the_floor_of_the_high_half(probe):
+    rng = random.Random(9)
+    lim = 1 << 63
+    su = [(-1, 1), (-(1 << 63), (1 << 63) - 1), ((1 << 63) - 1, (1 << 63) - 1), (-5, 7), (0, 12345)]
+    ss = [(-(1 << 63), -(1 << 63)), (-1, -1), ((1 << 63) - 1, -(1 << 63)), (-3, 5)]
+    uu = [((1 << 64) - 1, (1 << 64) - 1), (1 << 63, 2), (12345, 67890)]
+    for _ in range(300):
+        su.append((rng.randrange(-lim, lim), rng.randrange(0, lim)))
+        ss.append((rng.randrange(-lim, lim), rng.randrange(-lim, lim)))
+        uu.append((rng.randrange(0, 1 << 64), rng.randrange(0, 1 << 64)))
+    out = probe([f"mulsu {a} {b}" for a, b in su] + [f"mul {a} {b}" for a, b in ss] +
+                [f"umul {a} {b}" for a, b in uu])
+    want = [(a * b) >> 64 for a, b in su + ss + uu]                # Python >> floors
+    assert [int(x) for x in out] == want
