@@ -464,7 +464,9 @@ def run_adjoint(a):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     lx, ly, n, every, seed = 512, 1024, 500, 22, 5 + rank
-    p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
+    fix = a.precision == "fp64fix"   # forward steps with the fixed-point relaxation
+    p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
+                   precision=lbm.FP64_FIXED if fix else lbm.FP64)
     modes = I.rt_modes(lx, ly, seed)
 
     def forward_only():
@@ -502,9 +504,11 @@ def run_adjoint(a):
         line = {"metric": "D2Q37 MLUPS (gradient: forward + checkpointed adjoint)",
                 "value": whole_job_mlups(sites, n, world, t_grad * 1e3), "unit": "MLUPS", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_grad * 1e3 / n, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if fix else "f64",
+                "data": "synthetic",
                 "config": {"workload": f"dE/d(a_1..a_8, tau), E = kinetic energy after {n} steps of {lx}x{ly}",
-                           "checkpoint_every": every, "repeats": a.steps},
+                           "checkpoint_every": every, "repeats": a.steps,
+                           "forward_steps": "fixed-point relaxation" if fix else "float64"},
                 "forward_s": t_fwd, "gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

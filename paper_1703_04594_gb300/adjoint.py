@@ -8,6 +8,10 @@ the library's hand-written adjoint kernels (``lbm_adjoint_step``, ``lbm_init_adj
 example ``inputs.rt_fields`` with ``modes.a.requires_grad_()``) to get gradients with
 respect to interface-mode amplitudes.
 
+The forward steps (and their recomputation) run in the precision of ``params``: FP64, or
+FP64 with the fixed-point relaxation (LBM_FP64_FIXED, the same states within rounding);
+the adjoint steps are the FP64 ones either way.
+
 Memory: the forward pass keeps a checkpoint every ``every`` steps (default ceil(sqrt(N)));
 the backward pass recomputes each segment's states from its checkpoint, newest segment
 first, and walks the adjoint back through it.  Peak: ceil(N/every) + every + 3 states.
@@ -30,7 +34,7 @@ class _KineticEnergyAfter(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rho, ux, uy, T, tau, params, n_steps, every):
         p = dataclasses.replace(params, tau=float(tau))
-        if p.precision != lbm.FP64:
+        if p.precision not in (lbm.FP64, lbm.FP64_FIXED):
             raise ValueError("the adjoint runs on FP64 states")
         fields = [t.detach().contiguous() for t in (rho, ux, uy, T)]
         a, b = lbm.empty_state(p, rho.device), lbm.empty_state(p, rho.device)
@@ -52,13 +56,14 @@ class _KineticEnergyAfter(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_e):
         p, n_steps, every = ctx.p, ctx.n_steps, ctx.every
+        pa = dataclasses.replace(p, precision=lbm.FP64)  # the adjoint kernels (same states)
         dev = ctx.final.device
-        lam = lbm.empty_state(p, dev)
-        lbm.kinetic_energy_grad(p, ctx.final, lam)
+        lam = lbm.empty_state(pa, dev)
+        lbm.kinetic_energy_grad(pa, ctx.final, lam)
         lam.mul_(grad_e.to(dev))
-        lam_other = lbm.empty_state(p, dev)
+        lam_other = lbm.empty_state(pa, dev)
         dtau = torch.zeros((), dtype=torch.float64, device=dev)
-        work = lbm.adjoint_work(p, dev)
+        work = lbm.adjoint_work(pa, dev)
         starts = sorted(ctx.checkpoints)
         for k in reversed(starts):
             end = min(k + every, n_steps)
@@ -68,10 +73,10 @@ class _KineticEnergyAfter(torch.autograd.Function):
                 lbm.step(p, states[-1], nxt)
                 states.append(nxt)
             for n in reversed(range(k, end)):
-                lbm.adjoint_step(p, states[n - k], lam, lam_other, dtau, work)
+                lbm.adjoint_step(pa, states[n - k], lam, lam_other, dtau, work)
                 lam, lam_other = lam_other, lam
             del states
-        g = lbm.init_adjoint(p, *ctx.fields, lam)
+        g = lbm.init_adjoint(pa, *ctx.fields, lam)
         g_tau = None
         if ctx.tau_shape is not None:
             g_tau = dtau.to(ctx.tau_device).reshape(ctx.tau_shape)

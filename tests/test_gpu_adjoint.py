@@ -28,13 +28,13 @@ def _gpu():
     require_gpu()
 
 
-def gpu_energy_and_grad(lx, ly, seed, tau, steps, every=None, gx=0.0, gy=-1e-4):
+def gpu_energy_and_grad(lx, ly, seed, tau, steps, every=None, gx=0.0, gy=-1e-4, precision=lbm.FP64):
     m = I.rt_modes(lx, ly, seed)
     a = m.a.clone().requires_grad_(True)
     fields = I.rt_fields(lx, ly, I.RTModes(a=a, phi=m.phi), g=abs(gy))
     dev = [t.cuda() for t in fields]
     tau_t = torch.tensor(tau, dtype=torch.float64, requires_grad=True)
-    p = lbm.Params(lx, ly, tau=tau, gx=gx, gy=gy)
+    p = lbm.Params(lx, ly, tau=tau, gx=gx, gy=gy, precision=precision)
     e = A.kinetic_energy_after(*dev, tau_t, p, steps, every)
     e.backward()
     return float(e), a.grad.clone(), float(tau_t.grad)
@@ -98,6 +98,17 @@ def test_gradient_matches_oracle_reverse_mode_32x64_20_steps():
     scale = float(a.grad.abs().max())
     assert float((ga - a.grad).abs().max()) <= GRAD_TOL * scale, (ga, a.grad)
     assert abs(gt - float(tau_t.grad)) <= GRAD_TOL * abs(float(tau_t.grad)), (gt, float(tau_t.grad))
+
+
+def test_fixed_point_forward_gives_the_same_gradient():
+    """Forward steps with the fixed-point relaxation (LBM_FP64_FIXED) reach the same states
+    within rounding, so the checkpointed gradient is the same within 1e-9."""
+    args = (64, 128, 4, 0.8, 40)
+    e0, ga0, gt0 = gpu_energy_and_grad(*args, every=7)
+    e1, ga1, gt1 = gpu_energy_and_grad(*args, every=7, precision=lbm.FP64_FIXED)
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert float((ga1 - ga0).abs().max()) <= 1e-9 * float(ga0.abs().max())
+    assert abs(gt1 - gt0) <= 1e-9 * abs(gt0)
 
 
 def test_gradient_matches_finite_differences_512x1024_500_steps():
