@@ -243,6 +243,9 @@ def run_ours(a):
             lbm.collide(p, ftmp, dst, stream)
 
     bufs = [fa, fb]
+    # the float64 FMA rate measured by the library's probe kernel (TFLOP/s, FMA = 2 flops),
+    # beside the peak derived from unit counts and the maximum clock
+    fp64_measured = 2 * lbm.probe_peak(lbm.PROBE_DFMA) / 1e12 if not (fp32 or fix) else None
     for k in range(a.warmup):
         one_step(bufs[k % 2], bufs[(k + 1) % 2])
     torch.cuda.synchronize()
@@ -277,6 +280,8 @@ def run_ours(a):
         achieved = FLOPS_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(a.variant),
+                    "peak_measured": fp64_measured,
+                    "frac_of_measured": achieved / fp64_measured if fp64_measured else None,
                     "kernel": {"fused": "k_step_fp64", "separate": "whole step (3 kernels)",
                                "push": "whole step (3 kernels)", "aos": "k_step_layout<AoS>",
                                "psoa": "k_step_layout<PSoA>", "caosoa": "k_step_layout<CAoSoA>"}[a.variant],

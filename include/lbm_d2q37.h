@@ -247,6 +247,17 @@ int32_t lbm_batch_status(lbm_batch* b);
 int32_t lbm_batch_set_wait(lbm_batch* b, int64_t timeout_ns, int32_t phantom_arrivals);
 void lbm_batch_destroy(lbm_batch* b);
 
+/* ---- Peak probes: the roofline denominators of the arithmetic pipes, measured ----
+ * Runs a probe kernel on the current device (152 x 8 blocks of 256 threads, each thread
+ * 8 independent dependency chains of 4096 operations) and returns the sustained rate in
+ * *ops_per_second (operations, not flops: one FMA is one operation).  kind: 0 = float64
+ * FMA, 1 = float32 FMA, 2 = 32-bit integer multiply-add, 3 = signed 64 x 64 -> high 64
+ * product (__mul64hi), 4 = unsigned one.  Synchronous (device-wide); allocates and frees a
+ * small result buffer; returns LBM_EINVAL for another kind. */
+enum lbm_probe { LBM_PROBE_DFMA = 0, LBM_PROBE_FFMA = 1, LBM_PROBE_IMAD = 2, LBM_PROBE_MULHI64 = 3,
+                 LBM_PROBE_UMULHI64 = 4 };
+int32_t lbm_probe_peak(int32_t kind, double* ops_per_second);
+
 /* Human-readable text of an lbm_status code. */
 const char* lbm_strerror(int32_t status);
 /* The CUDA error code behind the most recent LBM_ECUDA on this thread (0 if none). */

@@ -100,6 +100,7 @@ _SIGS = {
     "lbm_batch_status": (ctypes.c_int32, [_VP]),
     "lbm_batch_set_wait": (ctypes.c_int32, [_VP, ctypes.c_int64, ctypes.c_int32]),
     "lbm_batch_destroy": (None, [_VP]),
+    "lbm_probe_peak": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
     "lbm_last_cuda_error": (ctypes.c_int32, []),
 }
@@ -405,3 +406,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+PROBE_DFMA, PROBE_FFMA, PROBE_IMAD, PROBE_MULHI64, PROBE_UMULHI64 = 0, 1, 2, 3, 4
+
+
+def probe_peak(kind: int) -> float:
+    """Measured sustained rate (operations per second, one FMA = one operation) of one
+    arithmetic pipe on the current device: the roofline denominators of the step kernels."""
+    out = ctypes.c_double()
+    _check("lbm_probe_peak", _lib().lbm_probe_peak(int(kind), ctypes.byref(out)))
+    return out.value
