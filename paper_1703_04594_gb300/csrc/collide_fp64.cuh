@@ -55,11 +55,6 @@ __device__ __forceinline__ long long to_fix52_e(double v, int& E) {
   return (x ^ s) - s;
 }
 
-__device__ __forceinline__ long long to_fix52(double v) {
-  int E;
-  return to_fix52_e(v, E);
-}
-
 // Streaming accumulation: each opposite pair is converted and added to the four sums
 // at once, so only the sums stay live (the products by the small integer velocity
 // weights are exact integer shifts and adds).  on_exp(i, E) sees the exponent field of

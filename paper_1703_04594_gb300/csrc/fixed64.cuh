@@ -35,7 +35,9 @@ __host__ __device__ __forceinline__ long long fx_from_double(double v, int k, in
   return (x ^ s) - s;
 }
 
-// X * 2^-k as a float64, rounded half up in magnitude; integer instructions only.
+// X * 2^-k as a float64, rounded half up in magnitude; integer instructions only.  (The
+// kernels use fx_to_double_dp below, which balances their pipes better; this form is the
+// integer-pipe alternative.)
 // Valid for 0 < 1086 - clz(|X|) - k < 2047 (normal results), which holds for every use here.
 __host__ __device__ __forceinline__ double fx_to_double(long long X, int k) {
   const long long s = X >> 63;
@@ -50,9 +52,7 @@ __host__ __device__ __forceinline__ double fx_to_double(long long X, int k) {
   const unsigned long long e = (unsigned long long)(1086 - lz - k - 1);
   unsigned long long bits = (e << 52) + mant;
   bits |= (unsigned long long)s & 0x8000000000000000ull;
-#ifndef LBM_FX_NO_ZERO_CHECK
   bits = A == 0 ? 0ull : bits;
-#endif
 #ifdef __CUDA_ARCH__
   return __longlong_as_double((long long)bits);
 #else

@@ -82,16 +82,6 @@ __device__ __forceinline__ void cp_async8(double* smem_dst, const double* gmem_s
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Conversion of the second population of each pair back to float64: on the integer pipes
-// (fx_to_double) or through the float64 pipe (fx_to_double_dp), whichever balances the
-// kernel's pipes better.
-#ifndef LBM_FIX64_TO_DOUBLE_MINUS
-#define LBM_FIX64_TO_DOUBLE_MINUS fx_to_double_dp
-#endif
-#ifndef LBM_FIX64_TO_DOUBLE_PLUS
-#define LBM_FIX64_TO_DOUBLE_PLUS fx_to_double_dp
-#endif
-
 template <bool B>
 struct BoolConst {
   static constexpr bool value = B;
@@ -242,7 +232,7 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     {
       constexpr int e = shell_exp(0);
       const long long K0 = fx_mulhi_su(A00, kCw(0)) * 2 + 1;
-      store(0, LBM_FIX64_TO_DOUBLE_PLUS(add_r(K0, fx_umulhi(om1u, sx[0])), 58 + e));
+      store(0, fx_to_double_dp(add_r(K0, fx_umulhi(om1u, sx[0])), 58 + e));
     }
     // K0 (58 bits) = w' (A00 + q A01 + q^2 A02), K1 (59) = w' (A10 + q A11),
     // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, K4 (62) = omega rho w' / 24,
@@ -274,8 +264,8 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
       const long long Ov = fx_mulhi(o1, s);                                     // 58
       const unsigned long long rp = fx_umulhi(om1u, sx[j * 32]);                // 63 + 59 -> 58
       const unsigned long long rm = fx_umulhi(om1u, sx[(j + NPAIR) * 32]);
-      store(j, LBM_FIX64_TO_DOUBLE_PLUS(add_r(Ev + Ov + 2, rp), 58 + e));
-      store(j + NPAIR, LBM_FIX64_TO_DOUBLE_MINUS(add_r(Ev - Ov + 1, rm), 58 + e));
+      store(j, fx_to_double_dp(add_r(Ev + Ov + 2, rp), 58 + e));
+      store(j + NPAIR, fx_to_double_dp(add_r(Ev - Ov + 1, rm), 58 + e));
     }
   };
   if (a.cc.om1 < 0.0) relax(BoolConst<true>());
