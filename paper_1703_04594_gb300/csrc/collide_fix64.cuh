@@ -2,23 +2,25 @@
 //
 // The same update as collide_site (Sec. 3, eq. "lbequation"; equilibrium and moments as in
 // collide_fp64.cuh), with a different split of the work between the GPU's pipes.  The site
-// scalars (moments, 1/rho, u, T, the gravity shift, the Hermite coefficients a_jk) stay in
-// float64.  Everything per shell and per population runs in signed 64-bit fixed point on
-// the integer pipes: the shell coefficients K0..K4 of omega rho w_s (C0 + C1 s + C2 s^2 +
-// s^3/6 + s^4/24), and for each opposite pair s = xi . u_s, s^2, the even part
-// E = K0 + s^2 (K2 + K4 s^2), the odd part O = s (K1 + K3 s^2) and
-// f_+/-' = (1 - omega) f_+/- + E +/- O.
+// scalars (moments, 1/rho, u, T and the gravity shift) stay in float64.  Everything after
+// them runs in signed 64-bit fixed point on the integer pipes: the Hermite coefficients
+// a_jk and their products with omega rho, the shell coefficients K0..K4 of
+// omega rho w_s (C0 + C1 s + C2 s^2 + s^3/6 + s^4/24), and for each opposite pair
+// s = xi . u_s, s^2, the even part E = K0 + s^2 (K2 + K4 s^2), the odd part
+// O = s (K1 + K3 s^2) and f_+/-' = (1 - omega) f_+/- + E +/- O.
 //
 // Formats.  Shell s is scaled by 2^e_s with w_s 2^e_s in [0.5, 1), so every scaled
 // population and coefficient is of order rho whatever the weight.  A product keeps the
 // high 64 bits of the 128-bit result (a truncation).  Each quantity has the number of
-// fraction bits that makes every product land on its consumer's binary point with no
-// shift: outputs, E, O and K0 have 58 (|v| < 32), K1 and 1 - omega times f 59 and 63,
-// K2 60, K3 61, K4 62, s 63 and s^2 62.  Each output carries a few units of 2^-58 relative
-// to its scaled size, below the 2^-53 rounding unit of a float64 result.  The truncations
-// (each -1/2 unit on average) are re-centred by small constant offsets to within half a
-// unit of 2^-58, far below the systematic error that the float64 weights themselves put on
-// mass conservation.
+// fraction bits that makes its products land on their consumers' binary points with no
+// shift:
+//   outputs, E, O, K0, (1 - omega) f   58  (|v| < 32)      K2, K2 + K4 s^2   60
+//   K1, K1 + K3 s^2                    59                  K3 61, K4 62
+//   s 63, s^2 62, |1 - omega| 63, f 59 + e_s
+// Each output carries a few units of 2^-58 relative to its scaled size, below the 2^-53
+// rounding unit of a float64 result.  The truncations (each -1/2 unit on average) are
+// re-centred by small constant offsets to within half a unit of 2^-58, far below the
+// systematic error that the float64 weights themselves put on mass conservation.
 //
 // Range.  The path is taken for sites with 0 <= f_i 2^e_s < 8 for all i,
 // 0 < omega rho < 3, |c u_s,x| and |c u_s,y| below 0.15 (so |s| < 0.6) and
@@ -34,9 +36,6 @@ __host__ __device__ constexpr int shell_exp(int s) {
   constexpr int t[8] = {2, 3, 4, 6, 7, 9, 11, 11};
   return t[s];
 }
-
-constexpr int FV = 58;  // scaled values: signed Q5.58
-constexpr int FU = 62;  // s, 1 - omega: signed Q1.62
 
 // Compile-time fixed-point constants from the model's float64 constants, computed exactly
 // in integers: a positive double is m 2^x with an integer m < 2^53.

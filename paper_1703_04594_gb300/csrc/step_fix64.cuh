@@ -4,16 +4,19 @@
 //   1. the 37 pull-gathered populations of the strip are copied global -> shared memory
 //      with cp.async (no registers held while the loads are in flight; inside a persistent
 //      kernel, whose sources were written earlier in the same launch, with L2 loads);
-//   2. moments: a rolled loop over opposite pairs reads shared memory and sums in 64-bit
-//      fixed point (collide_fp64.cuh), checking the range of the fixed-point path;
-//   3. site scalars in float64 (1/rho, u, T, gravity shift, Hermite coefficients);
-//   4. relaxation: a rolled loop over opposite pairs re-reads shared memory and evaluates
-//      the equilibrium polynomial and (1 - omega) f + omega f^eq in fixed point.
+//   2. a rolled loop over opposite pairs converts every population once to fixed point
+//      (written back over its float64 in shared memory), checks the range of the
+//      fixed-point path and sums the moments in 64-bit fixed point;
+//   3. the site scalars in float64 (1/rho, u, T, gravity shift);
+//   4. the Hermite coefficients and, per shell, K0..K4 in fixed point; then a rolled loop
+//      over opposite pairs reads the fixed-point populations and evaluates the equilibrium
+//      polynomial and (1 - omega) f + omega f^eq.
 // Rolled loops keep the kernel's code small: the fully unrolled form of this arithmetic is
 // ~8000 instructions per site, which thrashes the instruction cache.  Per-pair velocities
-// and shells, and per-shell constants, come from constant-memory tables.
-// Sites outside the fixed-point range take the float64 relaxation on the same staged values.
-// Warps next to a wall (two strips per column) run the float64 strip of step_fp64.cuh.
+// and shells, and per-shell constants, come from constant-memory tables.  Sites outside the
+// fixed-point range take the float64 collision on their values loaded again from global
+// memory; warps next to a wall (two strips per column) run the float64 strip of
+// step_fp64.cuh.
 #pragma once
 #include "collide_fix64.cuh"
 #include "step_fp64.cuh"

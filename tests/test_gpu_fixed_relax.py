@@ -119,3 +119,21 @@ def test_state_buffers_interchange_with_fp64():
     f = device_init(p, fields)
     rho, ux, uy, T = lbm.moments(p, f)
     assert rel_err(rho.cpu(), fields[0]) <= 1e-13 and rel_err(T.cpu(), fields[3]) <= 1e-13
+
+
+def test_full_size_sampled_columns():
+    """4096 x 8192 (the throughput lattice, seed 2) in the launch configuration the bench
+    times: two fixed-point steps on the GPU; the oracle recomputes sampled columns from
+    crops of +-6 columns (two steps reach 6 columns) built from the same seeded fields."""
+    p = lbm.Params(4096, 8192, precision=lbm.FP64_FIXED)
+    fields = rt_fields(p, seed=2)
+    res = run_fixed(p, fields, 2)
+    got = res[:, :, : p.ly]
+    for x in [0, 2047, 4095]:
+        cols = [(x + d) % p.lx for d in range(-6, 7)]
+        crop = [t[cols] for t in fields]
+        op = OL.Params(13, p.ly, tau=p.tau, gx=p.gx, gy=p.gy, t_bottom=p.t_bottom, t_top=p.t_top)
+        want = OL.run(OL.init_equilibrium(*crop), op, 2)[:, 6]
+        assert rel_err(got[:, x].double().cpu(), want) <= STEP_TOL, x
+    del res, got
+    torch.cuda.empty_cache()
