@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "../../include/lbm_d2q37.h"
+#include "adjoint_fix64.cuh"
 #include "kernels.h"
 #include "step_fp64.cuh"
 
@@ -94,6 +95,13 @@ __device__ __forceinline__ EqVjp eq_vjp_pairs(double rho, double usx, double usy
   return {Gr, rho * Gx, rho * Gy, rho * Gt};
 }
 
+// The float64 VJP for sites outside the fixed-point range, not inlined so that its
+// unrolled arithmetic does not weigh on the register allocation of the fixed-point path.
+__device__ __noinline__ EqVjp eq_vjp_float64(double rho, double usx, double usy, double t,
+                                             const double* __restrict__ lam, long long pop) {
+  return eq_vjp_pairs(rho, usx, usy, t, [&](int i) { return __ldg(lam + i * pop); });
+}
+
 __device__ __forceinline__ double block_sum_128(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -108,7 +116,7 @@ __device__ __forceinline__ double block_sum_128(double v) {
 
 // Step 1: per-site adjoint of the collision (block 32 x 4 as the forward kernels).
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128, 3) k_adj_collide(const double* __restrict__ fin,
+__global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict__ fin,
                                                      const double* __restrict__ lam_next, double* __restrict__ out,
                                                      double* __restrict__ dtau_part, StepArgs a, double tau, double gx,
                                                      double gy) {
@@ -137,7 +145,17 @@ __global__ void __launch_bounds__(128, 3) k_adj_collide(const double* __restrict
       double mu_ft = 0.0;  // sum_i mu_i f~_i
 #pragma unroll
       for (int i = 0; i < Q; ++i) mu_ft = fma(__ldg(lam + i * a.pop), f[i], mu_ft);
-      const EqVjp G = eq_vjp_pairs(rho, usx, usy, t, [&](int i) { return __ldg(lam + i * a.pop); });
+      // the VJP in fixed point (adjoint_fix64.cuh), in float64 outside its range
+      EqVjp G;
+      VjpSums V;
+      if (eq_vjp_sums_fix(usx, usy, t, [&](int i) { return __ldg(lam + i * a.pop); }, V)) {
+        G.Grho = V.Gr;
+        G.Gux = rho * fma(C, V.Ax, 2.0 * usx * V.Wu);
+        G.Guy = rho * fma(C, V.Ay, 2.0 * usy * V.Wu);
+        G.Gt = rho * V.Gt;
+      } else {
+        G = eq_vjp_float64(rho, usx, usy, t, lam, a.pop);
+      }
       const double nuE = G.Gt * inv / D;
       const double nuJx = G.Gux * inv - 2.0 * ux * G.Gt * inv / D;
       const double nuJy = G.Guy * inv - 2.0 * uy * G.Gt * inv / D;

@@ -115,6 +115,14 @@ __host__ __device__ constexpr unsigned long long kCw24(int s) {
   return t[s];
 }
 
+// round(2^64 / c^2), exact from the float64 c^2 = m 2^x
+__host__ __device__ constexpr unsigned long long inv_c2_64() {
+  const DoubleParts p = double_parts(C2);
+  const unsigned __int128 num = (unsigned __int128)1 << (64 - p.x);
+  return (unsigned long long)((num + p.m / 2) / p.m);
+}
+constexpr unsigned long long kInvC2 = inv_c2_64();
+
 // Positive float64 values order like their bit patterns.
 constexpr long long kBitsR = 0x4008000000000000LL;  // 3.0
 constexpr long long kBitsU = 0x3FC3333333333333LL;  // 0.15

@@ -50,14 +50,6 @@ static __constant__ ShellFix c_shell_fix[8] = {LBM_SHELL_FIX(0), LBM_SHELL_FIX(1
                                                LBM_SHELL_FIX(6), LBM_SHELL_FIX(7)};
 #undef LBM_SHELL_FIX
 
-// round(2^64 / c^2), exact from the float64 c^2 = m 2^x
-__host__ __device__ constexpr unsigned long long inv_c2_64() {
-  const DoubleParts p = double_parts(C2);
-  const unsigned __int128 num = (unsigned __int128)1 << (64 - p.x);
-  return (unsigned long long)((num + p.m / 2) / p.m);
-}
-constexpr unsigned long long kInvC2 = inv_c2_64();
-
 // x >> r with PTX semantics: shift amounts of 64 or more give 0.
 __device__ __forceinline__ unsigned long long shr_clamped(unsigned long long x, unsigned r) {
   unsigned long long y;
