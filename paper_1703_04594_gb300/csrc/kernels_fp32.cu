@@ -9,8 +9,11 @@
 namespace d2q37 {
 
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128, 6) k_step_fp32(const float* __restrict__ fin, float* __restrict__ fout,
-                                                   StepArgs a) {
+#ifndef LBM_FP32_MIN_BLOCKS
+#define LBM_FP32_MIN_BLOCKS 6  // 80 registers; measured best among 4..8 blocks per SM
+#endif
+__global__ void __launch_bounds__(128, LBM_FP32_MIN_BLOCKS) k_step_fp32(const float* __restrict__ fin,
+                                                                       float* __restrict__ fout, StepArgs a) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp
   step_strip_fp32<PERIODIC>(fin, fout, a, a, x, blockIdx.x * 32, LdReadOnly());
