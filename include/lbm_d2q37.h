@@ -19,13 +19,15 @@
  * Layout (structure of arrays, Sec. 4, "SoA"; y contiguous, two copies read and written
  * alternately): population i of site (x, y) is element  i*lx*pitch + x*pitch + y  of a
  * state buffer.  pitch = lbm_pitch(p) >= ly; elements y >= ly of a column are padding and
- * are never read.  FP64 states hold double f_i.  FP32_SHIFTED states hold float
+ * are never read.  FP64 and FP64_FIXED states hold double f_i.  FP32_SHIFTED states hold float
  * (f_i - w_i * rho0).  Population order: 0 = rest, 1..18 = the vectors returned by
  * lbm_model in that order, 18 + k = -(vector k).
  *
  * Conventions for every call:
  *   - Pointers named *_dev are device pointers; *_host are host pointers.  The caller
- *     owns every buffer and the stream; no entry point allocates device memory.
+ *     owns every buffer and the stream; no entry point allocates device memory except
+ *     lbm_batch_plan (its tables, freed by lbm_batch_destroy) and lbm_probe_peak (a result
+ *     buffer it frees before returning).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
  *     are stream-ordered and asynchronous unless stated otherwise.
  *   - Return value: LBM_OK, or an lbm_status error code.  Invalid arguments are
@@ -51,8 +53,8 @@ enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, L
  * evaluates the equilibrium polynomial and the relaxation of every population in 64-bit
  * fixed point on the integer pipes, with errors below one float64 rounding unit, for sites
  * in a stated physical range (float64 elsewhere).  lbm_step, lbm_run, lbm_init, lbm_moments,
- * lbm_kinetic_energy* and lbm_simulate_host accept it; the separate kernels, layouts,
- * adjoint and batch entry points take LBM_FP64. */
+ * lbm_kinetic_energy*, lbm_simulate_host and the batch entry points accept it; the separate
+ * kernels, layouts and adjoint entry points take LBM_FP64 (its states are the same). */
 enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_FIXED = 2 };
 enum lbm_bc { LBM_BC_WALLS = 0, LBM_BC_PERIODIC_Y = 1 /* test mode: y wraps like x */ };
 
@@ -205,9 +207,9 @@ int32_t lbm_init_adjoint(const lbm_params* p, const double* rho_dev, const doubl
 /* ---- Batched stepping of many independent lattices (uneven sizes, own tau, walls...) ----
  * The paper steps one lattice per process; this runs many independent problems in one
  * launch so that small lattices fill the GPU (its start-up mini-benchmark tuning, Sec. 6,
- * becomes the autotuner below).  All lattices of a batch share precision and bc mode; each
- * has its own lbm_params and its own two state buffers.  Results are bit-identical to
- * lbm_run on each lattice. */
+ * becomes the autotuner below).  All lattices of a batch share precision (LBM_FP64,
+ * LBM_FP64_FIXED or LBM_FP32_SHIFTED) and bc mode; each has its own lbm_params and its own
+ * two state buffers.  Results are bit-identical to lbm_run on each lattice. */
 typedef struct lbm_batch lbm_batch;
 enum lbm_batch_mode {
   LBM_BATCH_PER_STEP = 1,   /* one launch per step over every strip of every lattice */
@@ -216,8 +218,7 @@ enum lbm_batch_mode {
 };
 /* Validates n lattices and binds their buffers (f_a_dev[j], f_b_dev[j]: device states of
  * lbm_buffer_bytes(&params[j]) bytes, current state in f_a).  Allocates the batch's own
- * device descriptor table, tile table and barrier word (the only allocating entry point; freed by
- * lbm_batch_destroy).  Synchronous.  Default configuration: persistent, tiles of 32 x 4,
+ * device descriptor table, tile table and barrier word (freed by lbm_batch_destroy).  Synchronous.  Default configuration: persistent, tiles of 32 x 4,
  * as many blocks per SM as fit.  At most 65535 lattices. */
 int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a_dev, void* const* f_b_dev, int32_t n,
                        lbm_batch** out);
@@ -248,7 +249,7 @@ int32_t lbm_batch_set_wait(lbm_batch* b, int64_t timeout_ns, int32_t phantom_arr
 void lbm_batch_destroy(lbm_batch* b);
 
 /* ---- Peak probes: the roofline denominators of the arithmetic pipes, measured ----
- * Runs a probe kernel on the current device (152 x 8 blocks of 256 threads, each thread
+ * Runs a probe kernel on the current device (8 blocks of 256 threads per SM, each thread
  * 8 independent dependency chains of 4096 operations) and returns the sustained rate in
  * *ops_per_second (operations, not flops: one FMA is one operation).  kind: 0 = float64
  * FMA, 1 = float32 FMA, 2 = 32-bit integer multiply-add, 3 = signed 64 x 64 -> high 64
