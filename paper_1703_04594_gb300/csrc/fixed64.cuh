@@ -4,7 +4,8 @@
 // its integer pipes issue 64 operations per clock per SM.  A signed or unsigned 64 x 64 ->
 // high-64 product (a handful of IMAD instructions) then costs a fraction of one DFMA.  The
 // helpers below move values between float64 and signed 64-bit fixed point (value = X * 2^-k)
-// with integer instructions only, so no float64 conversion instruction is issued either.
+// with integer instructions, except fx_to_double_dp, which uses the float64 pipe's I2F on
+// purpose (that pipe is otherwise idle in the fixed-point kernels).
 #pragma once
 #include <stdint.h>
 
@@ -12,9 +13,9 @@ namespace d2q37 {
 
 // round(v * 2^k) for a float64 v, as a signed 64-bit integer; integer instructions only.
 // v * 2^k = m * 2^sh with m the 53-bit significand.  Left shifts (sh >= 0) are exact;
-// right shifts round half up.  `ovf` is set when sh > max_sh, i.e. when |v| * 2^k may
-// reach 2^(53 + max_sh); the caller picks max_sh so that its format cannot overflow.
-// Zeros and subnormals give 0.
+// right shifts round half away from zero.  The result is valid for sh <= 10, i.e.
+// |v| * 2^k < 2^63 (callers guarantee it); `ovf` is set when sh > max_sh, for callers that
+// check a tighter format bound instead.  Zeros and subnormals give 0.
 __host__ __device__ __forceinline__ long long fx_from_double(double v, int k, int max_sh, bool& ovf) {
 #ifdef __CUDA_ARCH__
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);

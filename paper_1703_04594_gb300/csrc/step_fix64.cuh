@@ -238,7 +238,7 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     {
       constexpr int e = shell_exp(0);
       const long long K0 = fx_mulhi_su(A00, kCw(0)) * 2 + 1;
-      store(0, fx_to_double_dp(add_r(K0, fx_umulhi(om1u, sx[0])), 58 + e));
+      store(0, fx_to_double_dp(add_r(K0 + (NEG ? 0 : 1), fx_umulhi(om1u, sx[0])), 58 + e));
     }
     // K0 (58 bits) = w' (A00 + q A01 + q^2 A02), K1 (59) = w' (A10 + q A11),
     // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, K4 (62) = omega rho w' / 24,
@@ -270,8 +270,10 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
       const long long Ov = fx_mulhi(o1, s);                                     // 58
       const unsigned long long rp = fx_umulhi(om1u, sx[j * 32]);                // 63 + 59 -> 58
       const unsigned long long rm = fx_umulhi(om1u, sx[(j + NPAIR) * 32]);
-      store(j, fx_to_double_dp(add_r(Ev + Ov + 2, rp), 58 + e));
-      store(j + NPAIR, fx_to_double_dp(add_r(Ev - Ov + 1, rm), 58 + e));
+      // re-centring: Ev, Ov and r each come out of a truncation 1/2 unit low on average,
+      // and r enters with the sign of 1 - omega
+      store(j, fx_to_double_dp(add_r(Ev + Ov + (NEG ? 1 : 2), rp), 58 + e));
+      store(j + NPAIR, fx_to_double_dp(add_r(Ev - Ov + (NEG ? 0 : 1), rm), 58 + e));
     }
   };
   if (a.cc.om1 < 0.0) relax(BoolConst<true>());
