@@ -138,3 +138,4 @@ def test_full_size_sampled_columns():
         assert rel_err(got[:, x].double().cpu(), want) <= STEP_TOL, x
     del res, got
     torch.cuda.empty_cache()
+
