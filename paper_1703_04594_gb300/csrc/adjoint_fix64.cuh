@@ -45,18 +45,6 @@ static __constant__ AdjShellFix c_adj_shell[8] = {LBM_ADJ_SHELL(0), LBM_ADJ_SHEL
                                                   LBM_ADJ_SHELL(6), LBM_ADJ_SHELL(7)};
 #undef LBM_ADJ_SHELL
 
-struct AdjPair {
-  int vx, vy, sh, pad;
-};
-#define LBM_ADJ_PAIR(j) \
-  { rep_vx(j), rep_vy(j), shell(j), 0 }
-static __constant__ AdjPair c_adj_pair[NPAIR + 1] = {
-    LBM_ADJ_PAIR(0),  LBM_ADJ_PAIR(1),  LBM_ADJ_PAIR(2),  LBM_ADJ_PAIR(3),  LBM_ADJ_PAIR(4),
-    LBM_ADJ_PAIR(5),  LBM_ADJ_PAIR(6),  LBM_ADJ_PAIR(7),  LBM_ADJ_PAIR(8),  LBM_ADJ_PAIR(9),
-    LBM_ADJ_PAIR(10), LBM_ADJ_PAIR(11), LBM_ADJ_PAIR(12), LBM_ADJ_PAIR(13), LBM_ADJ_PAIR(14),
-    LBM_ADJ_PAIR(15), LBM_ADJ_PAIR(16), LBM_ADJ_PAIR(17), LBM_ADJ_PAIR(18)};
-#undef LBM_ADJ_PAIR
-
 constexpr unsigned long long kInv6 = 3074457345618258603ull;   // round(2^64 / 6)
 constexpr unsigned long long kInv24 = 768614336404564651ull;   // round(2^64 / 24)
 
@@ -93,24 +81,12 @@ __device__ __forceinline__ bool eq_vjp_sums_fix(double usx, double usy, double t
   const int kmu = 1079 - (int)emax;  // |mu| < 2^(emax - 1022)  =>  |mu 2^kmu| < 2^57
   bool unused = false;
   const long long X1 = fx_from_double(Uxd, 63, 64, unused), Y1 = fx_from_double(Uyd, 63, 64, unused);
-  const long long t63 = fx_from_double(t, 63, 64, unused);
-  const unsigned long long ax = (unsigned long long)(X1 < 0 ? -X1 : X1), ay = (unsigned long long)(Y1 < 0 ? -Y1 : Y1);
-  // U = |u_s|^2 = (Ux^2 + Uy^2) / c^2 (62 fraction bits); products as in step_fix64.cuh
-  const long long U62 = (long long)fx_umulhi(fx_umulhi(ax, ax) + fx_umulhi(ay, ay), kInvC2);
-  const unsigned long long at = (unsigned long long)(t63 < 0 ? -t63 : t63);
-  const long long tU = fx_mulhi_su(t63, (unsigned long long)U62);                                // 61
-  const long long t2 = (long long)fx_umulhi(at, at);                                              // 62
-  const long long U2 = (long long)fx_umulhi((unsigned long long)U62, (unsigned long long)U62);    // 60
-  // coefficients in q of c0, c1, c2 (forward), dP/dU at s = 0 (b) and dP/dt at s = 0 (p):
-  //   c0 = a00 + a01 q + a02 q^2, c1 = a10 + a11 q, c2 = a20 + a21 q,
-  //   pue0 = b0 + b1 q, pt0 = p0 + p1 q + p2 q^2
-  const long long a00 = (1LL << 61) - (U62 >> 2) - (t63 >> 2) + (U2 >> 2) + tU + (t2 >> 1);  // 61
-  const long long a01 = t63 * 2 - tU * 4 - t2 * 8;                                               // 65
-  const long long a02 = t2 * 16;                                                                 // 69
-  const long long a10 = (1LL << 62) - (U62 >> 1) - t63;                                          // 62
-  const long long a11 = t63 * 2;                                                                 // 65
-  const long long a20 = (1LL << 62) - (U62 >> 1) - t63 - (t63 >> 1);                             // 63
-  const long long a21 = t63 * 2;                                                                 // 66
+  // the forward coefficients of c0, c1, c2 (collide_fix64.cuh), and those in q of dP/dU and
+  // dP/dt at s = 0:  pue0 = b0 + b1 q,  pt0 = p0 + p1 q + p2 q^2
+  const HermiteFix h = hermite_fix(X1, Y1, t);
+  const long long U62 = h.U62, t63 = h.t63;
+  const long long a00 = h.a00, a01 = h.a01, a02 = h.a02, a10 = h.a10, a11 = h.a11, a20 = h.a20;
+  const long long a21 = h.a11;                                                                   // 66
   const long long b0 = -(1LL << 60) + (U62 >> 3) + (t63 >> 2);                                   // 61
   const long long b1 = -t63;                                                                     // 65
   const long long p0 = -(1LL << 61) + (U62 >> 1) + (t63 >> 1);                                   // 61
@@ -140,7 +116,7 @@ __device__ __forceinline__ bool eq_vjp_sums_fix(double usx, double usy, double t
   }
 #pragma unroll 1
   for (int k = 1; k <= NPAIR; ++k) {
-    const AdjPair pk = c_adj_pair[k];
+    const PairFix pk = c_pair_fix[k];
     if (pk.sh != cur) {  // uniform across the warp
       if (cur > 0) flush();
       cur = pk.sh;

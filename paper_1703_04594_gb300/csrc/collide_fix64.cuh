@@ -123,6 +123,50 @@ __host__ __device__ constexpr unsigned long long inv_c2_64() {
 }
 constexpr unsigned long long kInvC2 = inv_c2_64();
 
+// Per-pair data of representatives 1..18 as a constant-memory table (one uniform load per
+// pair; cheaper in issue slots than unpacking the values from immediates).
+struct PairFix {
+  int vx, vy, v2, sh;
+};
+#define LBM_PAIR_FIX(j) \
+  { rep_vx(j), rep_vy(j), rep_vx(j) * rep_vx(j) + rep_vy(j) * rep_vy(j), shell(j) }
+static __constant__ PairFix c_pair_fix[NPAIR + 1] = {
+    LBM_PAIR_FIX(0),  LBM_PAIR_FIX(1),  LBM_PAIR_FIX(2),  LBM_PAIR_FIX(3),  LBM_PAIR_FIX(4),
+    LBM_PAIR_FIX(5),  LBM_PAIR_FIX(6),  LBM_PAIR_FIX(7),  LBM_PAIR_FIX(8),  LBM_PAIR_FIX(9),
+    LBM_PAIR_FIX(10), LBM_PAIR_FIX(11), LBM_PAIR_FIX(12), LBM_PAIR_FIX(13), LBM_PAIR_FIX(14),
+    LBM_PAIR_FIX(15), LBM_PAIR_FIX(16), LBM_PAIR_FIX(17), LBM_PAIR_FIX(18)};
+#undef LBM_PAIR_FIX
+
+// The Hermite coefficients of C0 = a00 + a01 q + a02 q^2, C1 = a10 + a11 q, C2 = a20 + a21 q
+// (collide_fp64.cuh) in fixed point, from X1 = c u_s,x and Y1 = c u_s,y (63 fraction bits)
+// and t = T_s - 1, each with the fraction bits (in brackets) that its size allows in the
+// range of the fixed-point path (|X1|, |Y1| < 0.15, |t| < 0.25):
+//   a00 = 1 - U/2 - t + U^2/8 + tU + t^2 [61]   a01 = t/2 - tU/4 - t^2 [65]   a02 = t^2/8 [69]
+//   a10 = 1 - U/2 - 2t [62]   a11 = t/2 [65]   a20 = 1/2 - U/4 - 3t/2 [63]   a21 = t/4 [66]
+// with U = |u_s|^2 = (Ux^2 + Uy^2) / c^2 [62]; a21 is the same integer as a11.
+struct HermiteFix {
+  long long U62, t63, a00, a01, a02, a10, a11, a20;
+};
+
+__device__ __forceinline__ HermiteFix hermite_fix(long long X1, long long Y1, double t) {
+  bool unused = false;
+  HermiteFix h;
+  h.t63 = fx_from_double(t, 63, 64, unused);
+  const unsigned long long ax = (unsigned long long)(X1 < 0 ? -X1 : X1), ay = (unsigned long long)(Y1 < 0 ? -Y1 : Y1);
+  h.U62 = (long long)fx_umulhi(fx_umulhi(ax, ax) + fx_umulhi(ay, ay), kInvC2);
+  const unsigned long long at = (unsigned long long)(h.t63 < 0 ? -h.t63 : h.t63);
+  const long long tU = fx_mulhi_su(h.t63, (unsigned long long)h.U62);                             // 61
+  const long long t2 = (long long)fx_umulhi(at, at);                                                // 62
+  const long long U2 = (long long)fx_umulhi((unsigned long long)h.U62, (unsigned long long)h.U62);  // 60
+  h.a00 = (1LL << 61) - (h.U62 >> 2) - (h.t63 >> 2) + (U2 >> 2) + tU + (t2 >> 1);
+  h.a01 = h.t63 * 2 - tU * 4 - t2 * 8;
+  h.a02 = t2 * 16;
+  h.a10 = (1LL << 62) - (h.U62 >> 1) - h.t63;
+  h.a11 = h.t63 * 2;
+  h.a20 = (1LL << 62) - (h.U62 >> 1) - h.t63 - (h.t63 >> 1);
+  return h;
+}
+
 // Positive float64 values order like their bit patterns.
 constexpr long long kBitsR = 0x4008000000000000LL;  // 3.0
 constexpr long long kBitsU = 0x3FC3333333333333LL;  // 0.15

@@ -23,20 +23,6 @@
 
 namespace d2q37 {
 
-// Per-pair data of representatives 1..18 as a constant-memory table (one uniform load per
-// pair; cheaper in issue slots than unpacking the values from immediates).
-struct PairFix {
-  int vx, vy, v2, sh;
-};
-#define LBM_PAIR_FIX(j) \
-  { rep_vx(j), rep_vy(j), rep_vx(j) * rep_vx(j) + rep_vy(j) * rep_vy(j), shell(j) }
-static __constant__ PairFix c_pair_fix[NPAIR + 1] = {
-    LBM_PAIR_FIX(0),  LBM_PAIR_FIX(1),  LBM_PAIR_FIX(2),  LBM_PAIR_FIX(3),  LBM_PAIR_FIX(4),
-    LBM_PAIR_FIX(5),  LBM_PAIR_FIX(6),  LBM_PAIR_FIX(7),  LBM_PAIR_FIX(8),  LBM_PAIR_FIX(9),
-    LBM_PAIR_FIX(10), LBM_PAIR_FIX(11), LBM_PAIR_FIX(12), LBM_PAIR_FIX(13), LBM_PAIR_FIX(14),
-    LBM_PAIR_FIX(15), LBM_PAIR_FIX(16), LBM_PAIR_FIX(17), LBM_PAIR_FIX(18)};
-#undef LBM_PAIR_FIX
-
 struct ShellFix {
   long long cw, cq, cq2;
   unsigned long long cw6, cw24;
@@ -207,31 +193,14 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   // relaxation loop below is instantiated for each sign and multiplies unsigned values
   const unsigned long long om1u = (unsigned long long)fx_from_double(fabs(a.cc.om1), 63, 64, unused);
   const long long X1 = fx_from_double(v.Ux, 63, 64, unused), Y1 = fx_from_double(v.Uy, 63, 64, unused);
-  const long long t63 = fx_from_double(v.t, 63, 64, unused);                    // |t| < 0.25
-  // U = |u_s|^2 = (Ux^2 + Uy^2) / c^2 (62 bits), and the products of the Hermite coefficients
-  const unsigned long long ax = (unsigned long long)(X1 < 0 ? -X1 : X1), ay = (unsigned long long)(Y1 < 0 ? -Y1 : Y1);
-  const long long U62 = (long long)fx_umulhi(fx_umulhi(ax, ax) + fx_umulhi(ay, ay), kInvC2);
-  const unsigned long long at = (unsigned long long)(t63 < 0 ? -t63 : t63);
-  const long long tU = fx_mulhi_su(t63, (unsigned long long)U62);              // 61
-  const long long t2 = (long long)fx_umulhi(at, at);                            // 62
-  const long long U2 = (long long)fx_umulhi((unsigned long long)U62, (unsigned long long)U62);  // 60
-  // a_jk of C0 = a00 + a01 q + a02 q^2, C1 = a10 + a11 q, C2 = a20 + a21 q (collide_fp64.cuh),
-  // each with the fraction bits (in brackets) that its size allows:
-  //   a00 = 1 - U/2 - t + U^2/8 + tU + t^2 [61]   a01 = t/2 - tU/4 - t^2 [65]   a02 = t^2/8 [69]
-  //   a10 = 1 - U/2 - 2t [62]   a11 = t/2 [65]   a20 = 1/2 - U/4 - 3t/2 [63]   a21 = t/4 [66]
-  const long long a00 = (1LL << 61) - (U62 >> 2) - (t63 >> 2) + (U2 >> 2) + tU + (t2 >> 1);
-  const long long a01 = t63 * 2 - tU * 4 - t2 * 8;
-  const long long a02 = t2 * 16;
-  const long long a10 = (1LL << 62) - (U62 >> 1) - t63;
-  const long long a11 = t63 * 2;  // also a21, at 66 bits
-  const long long a20 = (1LL << 62) - (U62 >> 1) - t63 - (t63 >> 1);
+  const HermiteFix h = hermite_fix(X1, Y1, v.t);
   // A = omega rho a (the product with R at 61 bits takes 3 off each)
-  const long long A00 = fx_mulhi_su(a00, Rf);  // 58
-  const long long A01 = fx_mulhi_su(a01, Rf);  // 62
-  const long long A02 = fx_mulhi_su(a02, Rf);  // 66
-  const long long A10 = fx_mulhi_su(a10, Rf);  // 59
-  const long long A11 = fx_mulhi_su(a11, Rf);  // 62 (A21: the same integer at 63)
-  const long long A20 = fx_mulhi_su(a20, Rf);  // 60
+  const long long A00 = fx_mulhi_su(h.a00, Rf);  // 58
+  const long long A01 = fx_mulhi_su(h.a01, Rf);  // 62
+  const long long A02 = fx_mulhi_su(h.a02, Rf);  // 66
+  const long long A10 = fx_mulhi_su(h.a10, Rf);  // 59
+  const long long A11 = fx_mulhi_su(h.a11, Rf);  // 62 (A21: the same integer at 63)
+  const long long A20 = fx_mulhi_su(h.a20, Rf);  // 60
   const auto relax = [&](auto neg) {
     constexpr bool NEG = decltype(neg)::value;
     const auto add_r = [](long long v, unsigned long long r) { return NEG ? v - (long long)r : v + (long long)r; };
