@@ -375,7 +375,7 @@ def run_ours(a):
                 "gpu_launches": a.steps * (3 if separate else 1),
                 "clocks": clk.summary()}
         if not a.no_cpu_baseline and world == 1 and (lx, ly) == (LX, LY):
-            line["cpu_baseline"] = oracle_sample(4)
+            line["cpu_baseline"] = oracle_sample(16)   # ~14 s of CPU work on 16 cores
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
