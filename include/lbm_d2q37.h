@@ -188,7 +188,8 @@ int32_t lbm_step_layout(const lbm_params* p, int32_t layout, const void* f_in_de
  * The paper steps forward only; these are the transposed Jacobians of the same operations
  * (propagate and bc are linear, collide is differentiated site by site through the
  * moments of eq. "macro", the gravity shift and the Hermite equilibrium).  FP64 only. */
-/* Bytes of workspace lbm_adjoint_step needs: one state buffer plus per-tile partials. */
+/* Bytes of workspace lbm_adjoint_step needs: 2 * lx * 26 doubles of wall slots (the
+ * adjoint values fed from ghost rows, per wall and source column) plus per-tile partials. */
 int64_t lbm_adjoint_work_bytes(const lbm_params* p);
 /* lam_n = (d step / d f_n)^T lam_next, and *dtau_accum += lam_next . d step(f_n) / d tau
  * (deterministic per-tile partials summed in a fixed order).  f_n is the state the forward

@@ -5,7 +5,7 @@
 // is rho_w(x_s) * w_i P_i(T_wall), rho_w a sum of the source column's wall-row
 // populations); collide C acts site by site (Sec. 3, eqs. "lbequation", "macro").  For
 // lambda' = dL/df^{n+1}:
-//   1. (k_adj_collide) at every site, recompute f~ = B P f^n and its moments, then
+//   1. (k_adj_collide) at every site z, recompute f~ = B P f^n and its moments, then
 //        mu_i = lambda'_i,
 //        out_i = (1 - w) mu_i + w (nu_rho + nu_J . xi_i + nu_E |xi_i|^2),   w = 1/tau,
 //      where nu = (d f^eq / d(rho, J, E))^T mu through u = J/rho,
@@ -13,10 +13,14 @@
 //      and the fourth-order Hermite polynomial; the site's contribution to dL/dtau is
 //        sum_i mu_i d f_i'/d tau = -(1/tau^2) sum_i mu_i (f^eq_i - f~_i)
 //                                   + w [G_u . g + G_t (1 - 2 tau) |g|^2 / D];
-//   2. (k_adj_propagate) lambda_i(x, y) = out_i(x + v_i) for destinations inside the fluid
-//      (the transpose of the pull), plus, on the wall rows, the transpose of the ghost
-//      values: every population of (x_s, 0) receives sum over the ghost-fed entries
-//      (x_s + vx_i, y') of out_i(x_s + vx_i, y') * w_i P_i(T_bottom), and likewise at the top.
+//      and the transpose of the pull is applied on the way out, as a push: out_i(z) is
+//      the value of lambda_i(z - v_i) when z - v_i is a fluid site.  When it is a ghost
+//      (z was fed from the wall), out_i(z) times the ghost's weight w_i P_i(T_wall) goes
+//      to a per-column slot of the wall's source column instead; entries lambda_i(x) with
+//      no fluid source x + v_i are set to zero by their own site;
+//   2. (k_adj_walls) the wall rows: every population of (x_s, 0) receives the sum of the
+//      bottom slots of column x_s (the transpose of rho_w = sum_j f_j(x_s, 0)), and
+//      likewise at the top.
 // dL/dtau partials are summed per block and then in a fixed order (deterministic).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -112,14 +116,53 @@ __device__ __forceinline__ double block_sum_128(double v) {
   return (ws[0] + ws[1]) + (ws[2] + ws[3]);
 }
 
+// Ghost slots of one column: population i with vy_i > 0 fed rows 0 .. vy_i - 1 of column
+// x_s + vx_i from the bottom ghosts of column x_s; those entries take bottom slots
+// ghost_base(i, +1) + row of column x_s.  The top mirrors it with -vy_i and row ly - 1 - y.
+__host__ __device__ constexpr int ghost_base_calc(int i, int sign) {
+  int n = 0;
+  for (int j = 0; j < i; ++j) n += sign * vy(j) > 0 ? sign * vy(j) : 0;
+  return n;
+}
+constexpr int kGhostSlots = ghost_base_calc(Q, 1);  // 26 for D2Q37, the same at the top
+static_assert(ghost_base_calc(Q, -1) == kGhostSlots, "the velocity set is symmetric in y");
+__host__ __device__ constexpr int ghost_base(int i, int sign) {
+  constexpr int b[Q] = {ghost_base_calc(0, 1),  ghost_base_calc(1, 1),  ghost_base_calc(2, 1),  ghost_base_calc(3, 1),
+                        ghost_base_calc(4, 1),  ghost_base_calc(5, 1),  ghost_base_calc(6, 1),  ghost_base_calc(7, 1),
+                        ghost_base_calc(8, 1),  ghost_base_calc(9, 1),  ghost_base_calc(10, 1), ghost_base_calc(11, 1),
+                        ghost_base_calc(12, 1), ghost_base_calc(13, 1), ghost_base_calc(14, 1), ghost_base_calc(15, 1),
+                        ghost_base_calc(16, 1), ghost_base_calc(17, 1), ghost_base_calc(18, 1), ghost_base_calc(19, 1),
+                        ghost_base_calc(20, 1), ghost_base_calc(21, 1), ghost_base_calc(22, 1), ghost_base_calc(23, 1),
+                        ghost_base_calc(24, 1), ghost_base_calc(25, 1), ghost_base_calc(26, 1), ghost_base_calc(27, 1),
+                        ghost_base_calc(28, 1), ghost_base_calc(29, 1), ghost_base_calc(30, 1), ghost_base_calc(31, 1),
+                        ghost_base_calc(32, 1), ghost_base_calc(33, 1), ghost_base_calc(34, 1), ghost_base_calc(35, 1),
+                        ghost_base_calc(36, 1)};
+  constexpr int t[Q] = {ghost_base_calc(0, -1),  ghost_base_calc(1, -1),  ghost_base_calc(2, -1),  ghost_base_calc(3, -1),
+                        ghost_base_calc(4, -1),  ghost_base_calc(5, -1),  ghost_base_calc(6, -1),  ghost_base_calc(7, -1),
+                        ghost_base_calc(8, -1),  ghost_base_calc(9, -1),  ghost_base_calc(10, -1), ghost_base_calc(11, -1),
+                        ghost_base_calc(12, -1), ghost_base_calc(13, -1), ghost_base_calc(14, -1), ghost_base_calc(15, -1),
+                        ghost_base_calc(16, -1), ghost_base_calc(17, -1), ghost_base_calc(18, -1), ghost_base_calc(19, -1),
+                        ghost_base_calc(20, -1), ghost_base_calc(21, -1), ghost_base_calc(22, -1), ghost_base_calc(23, -1),
+                        ghost_base_calc(24, -1), ghost_base_calc(25, -1), ghost_base_calc(26, -1), ghost_base_calc(27, -1),
+                        ghost_base_calc(28, -1), ghost_base_calc(29, -1), ghost_base_calc(30, -1), ghost_base_calc(31, -1),
+                        ghost_base_calc(32, -1), ghost_base_calc(33, -1), ghost_base_calc(34, -1), ghost_base_calc(35, -1),
+                        ghost_base_calc(36, -1)};
+  return sign > 0 ? b[i] : t[i];
+}
+
 }  // namespace
 
-// Step 1: per-site adjoint of the collision (block 32 x 4 as the forward kernels).
+// Step 1: per-site adjoint of the collision with the transposed propagate as its store
+// (block 32 x 4 as the forward kernels).  `side` holds 2 * lx * kGhostSlots doubles: the
+// bottom slots of every column, then the top slots.
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict__ fin,
-                                                     const double* __restrict__ lam_next, double* __restrict__ out,
-                                                     double* __restrict__ dtau_part, StepArgs a, double tau, double gx,
-                                                     double gy) {
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const double* __restrict__ fin,
+                                                     const double* __restrict__ lam_next, double* __restrict__ lam_out,
+                                                     double* __restrict__ side, double* __restrict__ dtau_part,
+                                                     StepArgs a, double tau, double gx, double gy) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   const int y0 = blockIdx.x * 32;
   const int y = y0 + threadIdx.x;
@@ -161,13 +204,39 @@ __global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict
       const double nuJy = G.Guy * inv - 2.0 * uy * G.Gt * inv / D;
       const double nuR = G.Grho - (G.Gux * ux + G.Guy * uy) * inv + G.Gt * (-E * inv + 2.0 * uu) * inv / D;
       const double om = 1.0 / tau, om1 = 1.0 - om;
-      __stcs(out + o, fma(om1, __ldg(lam), om * nuR));
+      // out_i(z) is lambda_i(z - v_i) of the previous step (the transposed pull), or the
+      // wall slot of its source column when z - v_i is a ghost
+      const auto push = [&](int i, double val) {
+        const int xs = wrap_index(x - vx(i), a.lx), yd = y - vy(i);
+        if (PERIODIC) {
+          __stcs(lam_out + i * a.pop + (long long)xs * a.pitch + wrap_index(yd, a.ly), val);
+        } else if (yd < 0) {
+          side[(long long)xs * kGhostSlots + ghost_base(i, 1) + y] = val * a.wall_b[i];
+        } else if (yd >= a.ly) {
+          side[((long long)a.lx + xs) * kGhostSlots + ghost_base(i, -1) + (a.ly - 1 - y)] = val * a.wall_t[i];
+        } else {
+          __stcs(lam_out + i * a.pop + (long long)xs * a.pitch + yd, val);
+        }
+      };
+      // out_{+-v} = (1-w) mu + A_s +- B_v with A_s = w (nuR + nuE c^2 |v|^2) (one per shell)
+      // and B_v = w c nuJ . v (from the multiples of w c nuJ)
+      const double wR = om * nuR, wE = om * (C2 * nuE);
+      const Multiples wJ = make_multiples(om * (C * nuJx), om * (C * nuJy));
+      push(0, fma(om1, __ldg(lam), wR));
 #pragma unroll
-      for (int k = 1; k <= NPAIR; ++k) {  // out_{+-v} = (1-w) mu + w (nuR + nuE q +- nuJ . xi)
-        const double A = fma(nuE, C2 * (double)v2(k), nuR);
-        const double B = fma(nuJx, C * (double)rep_vx(k), nuJy * (C * (double)rep_vy(k)));
-        __stcs(out + o + k * a.pop, fma(om1, __ldg(lam + k * a.pop), om * (A + B)));
-        __stcs(out + o + (k + NPAIR) * a.pop, fma(om1, __ldg(lam + (k + NPAIR) * a.pop), om * (A - B)));
+      for (int k = 1; k <= NPAIR; ++k) {
+        const double A = fma(wE, (double)v2(k), wR);
+        const double B = dot_v(wJ, rep_vx(k), rep_vy(k));
+        push(k, fma(om1, __ldg(lam + k * a.pop), A + B));
+        push(k + NPAIR, fma(om1, __ldg(lam + (k + NPAIR) * a.pop), A - B));
+      }
+      // entries of this site whose source z + v_i lies beyond a wall get no push
+      if (!PERIODIC && (y < 3 || y >= a.ly - 3)) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int ys = y + vy(i);
+          if (ys < 0 || ys >= a.ly) __stcs(lam_out + i * a.pop + o, 0.0);
+        }
       }
       // sum_i mu_i f^eq_i = rho * Grho
       contrib = -(rho * G.Grho - mu_ft) * om * om + om * (G.Gux * gx + G.Guy * gy + G.Gt * (1.0 - 2.0 * tau) * gg / D);
@@ -177,47 +246,22 @@ __global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict
   if (threadIdx.x == 0 && threadIdx.y == 0) dtau_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
-// Step 2: transpose of pull propagate + wall bc.  One thread per site.
-template <bool PERIODIC>
-__global__ void __launch_bounds__(128) k_adj_propagate(const double* __restrict__ out, double* __restrict__ lam,
-                                                       StepArgs a) {
-  const int x = blockIdx.y * 4 + threadIdx.y;
-  const int y = blockIdx.x * 32 + threadIdx.x;
-  if (x >= a.lx || y >= a.ly) return;
+// Step 2: the wall rows' share of the transposed bc, after step 1 has written every
+// lambda entry: lambda_j(x, 0) += sum of the bottom slots of column x for all j (the ghost
+// values' dependence on rho_w(x) = sum_j f_j(x, 0)), and likewise for row ly - 1.  One
+// thread per column and wall (blockIdx.y: 0 bottom, 1 top).
+__global__ void __launch_bounds__(128) k_adj_walls(const double* __restrict__ side, double* __restrict__ lam,
+                                                   StepArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.lx) return;
+  const int top = blockIdx.y;
+  const double* src = side + ((long long)top * a.lx + x) * kGhostSlots;
   double wall = 0.0;
-  if (!PERIODIC && y == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (vy(i) <= 0) continue;
-      const double* src = out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch;
-      double s = 0.0;
-      for (int yp = 0; yp < vy(i) && yp < a.ly; ++yp) s += __ldg(src + yp);
-      wall = fma(s, a.wall_b[i], wall);
-    }
-  }
-  if (!PERIODIC && y == a.ly - 1) {
+  for (int k = 0; k < kGhostSlots; ++k) wall += src[k];
+  double* dst = lam + (long long)x * a.pitch + (top ? a.ly - 1 : 0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (vy(i) >= 0) continue;
-      const double* src = out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch;
-      double s = 0.0;
-      for (int yp = a.ly + vy(i); yp < a.ly; ++yp) s += __ldg(src + yp);
-      wall = fma(s, a.wall_t[i], wall);
-    }
-  }
-  double* dst = lam + (long long)x * a.pitch + y;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    int yd = y + vy(i);
-    double v = 0.0;
-    if (PERIODIC) {
-      yd = wrap_index(yd, a.ly);
-      v = __ldg(out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch + yd);
-    } else if (yd >= 0 && yd < a.ly) {
-      v = __ldg(out + i * a.pop + (long long)wrap_index(x + vx(i), a.lx) * a.pitch + yd);
-    }
-    __stcs(dst + i * a.pop, v + wall);
-  }
+  for (int i = 0; i < Q; ++i) dst[i * a.pop] += wall;
 }
 
 // Adds sum(part[0..n)) to *acc in a fixed order (one block).
@@ -278,15 +322,16 @@ long long adjoint_partial_count(const StepArgs& a) {
   return (long long)g.x * g.y;
 }
 
-cudaError_t launch_adjoint_step(const double* fin, const double* lam_next, double* lam, double* out, double* part,
+long long adjoint_side_count(const StepArgs& a) { return 2LL * a.lx * kGhostSlots; }
+
+cudaError_t launch_adjoint_step(const double* fin, const double* lam_next, double* lam, double* side, double* part,
                                 double* dtau, const StepArgs& a, double tau, double gx, double gy, cudaStream_t s) {
   const dim3 blk(32, 4);
   if (a.periodic) {
-    k_adj_collide<true><<<site_grid(a), blk, 0, s>>>(fin, lam_next, out, part, a, tau, gx, gy);
-    k_adj_propagate<true><<<site_grid(a), blk, 0, s>>>(out, lam, a);
+    k_adj_collide<true><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, tau, gx, gy);
   } else {
-    k_adj_collide<false><<<site_grid(a), blk, 0, s>>>(fin, lam_next, out, part, a, tau, gx, gy);
-    k_adj_propagate<false><<<site_grid(a), blk, 0, s>>>(out, lam, a);
+    k_adj_collide<false><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, tau, gx, gy);
+    k_adj_walls<<<dim3((a.lx + 127) / 128, 2), 128, 0, s>>>(side, lam, a);
   }
   k_reduce_add<<<1, 256, 0, s>>>(part, adjoint_partial_count(a), dtau);
   return cudaGetLastError();
@@ -322,7 +367,7 @@ extern "C" {
 int64_t lbm_adjoint_work_bytes(const lbm_params* p) {
   if (!params_valid(p) || p->precision != LBM_FP64) return -1;
   const StepArgs a = make_step_args(p);
-  return lbm_buffer_bytes(p) + adjoint_partial_count(a) * (int64_t)sizeof(double);
+  return (adjoint_side_count(a) + adjoint_partial_count(a)) * (int64_t)sizeof(double);
 }
 
 int32_t lbm_adjoint_step(const lbm_params* p, const void* f_n, const void* lam_next, void* lam_n, double* dtau_accum,
@@ -333,9 +378,9 @@ int32_t lbm_adjoint_step(const lbm_params* p, const void* f_n, const void* lam_n
   const int64_t need = lbm_adjoint_work_bytes(p);
   if ((int64_t)work_bytes < need || lam_next == lam_n || f_n == lam_n) return LBM_EINVAL;
   const StepArgs a = make_step_args(p);
-  double* out = (double*)work;
-  double* part = (double*)((char*)work + lbm_buffer_bytes(p));
-  return status_of(launch_adjoint_step((const double*)f_n, (const double*)lam_next, (double*)lam_n, out, part,
+  double* side = (double*)work;
+  double* part = side + adjoint_side_count(a);
+  return status_of(launch_adjoint_step((const double*)f_n, (const double*)lam_next, (double*)lam_n, side, part,
                                        dtau_accum, a, p->tau, p->gx, p->gy, (cudaStream_t)stream));
 }
 

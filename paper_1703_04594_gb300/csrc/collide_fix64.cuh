@@ -4,18 +4,18 @@
 // collide_fp64.cuh), with a different split of the work between the GPU's pipes.  The site
 // scalars (moments, 1/rho, u, T and the gravity shift) stay in float64.  Everything after
 // them runs in signed 64-bit fixed point on the integer pipes: the Hermite coefficients
-// a_jk and their products with omega rho, the shell coefficients K0..K4 of
+// a_jk and their products with omega rho, the shell coefficients K0..K3 of
 // omega rho w_s (C0 + C1 s + C2 s^2 + s^3/6 + s^4/24), and for each opposite pair
-// s = xi . u_s, s^2, the even part E = K0 + s^2 (K2 + K4 s^2), the odd part
-// O = s (K1 + K3 s^2) and f_+/-' = (1 - omega) f_+/- + E +/- O.
+// s = xi . u_s, s^2, h = K3 s^2, the odd part O = s (K1 + h), the even part
+// E = K0 + s^2 (K2 + h/4) and f_+/-' = (1 - omega) f_+/- + E +/- O.
 //
 // Formats.  Shell s is scaled by 2^e_s with w_s 2^e_s in [0.5, 1), so every scaled
 // population and coefficient is of order rho whatever the weight.  A product keeps the
 // high 64 bits of the 128-bit result (a truncation).  Each quantity has the number of
 // fraction bits that makes its products land on their consumers' binary points with no
 // shift:
-//   outputs, E, O, K0, (1 - omega) f   58  (|v| < 32)      K2, K2 + K4 s^2   60
-//   K1, K1 + K3 s^2                    59                  K3 61, K4 62
+//   outputs, E, O, K0, (1 - omega) f   58  (|v| < 32)      K2, K2 + h/4      60
+//   K1, h = K3 s^2, K1 + h             59                  K3 61
 //   s 63, s^2 62, |1 - omega| 63, f 59 + e_s
 // Each output carries a few units of 2^-58 relative to its scaled size, below the 2^-53
 // rounding unit of a float64 result.  The truncations (each -1/2 unit on average) are
@@ -60,7 +60,7 @@ __host__ __device__ constexpr unsigned long long fx_const(double a, double b, in
 }
 // Shell constants with w' = w_s 2^e_s (signed formats need values below 2^63):
 //   cw = w' (Q0.63), cq = w' q_s (Q4.59), cq2 = w' q_s^2 (Q8.55, with q_s^2 rounded to
-//   64 bits first), cw6 = w' / 6 and cw24 = w' / 24 (unsigned Q0.64).
+//   64 bits first), cw6 = w' / 6 (unsigned Q0.64).
 __host__ __device__ constexpr long long shell_cw(int s) {
   return (long long)fx_const(w_shell(s), 1.0, shell_exp(s) + 63);
 }
@@ -106,12 +106,6 @@ __host__ __device__ constexpr unsigned long long kCw6(int s) {
   constexpr unsigned long long t[8] = {shell_cw_div(0, 6), shell_cw_div(1, 6), shell_cw_div(2, 6),
                                        shell_cw_div(3, 6), shell_cw_div(4, 6), shell_cw_div(5, 6),
                                        shell_cw_div(6, 6), shell_cw_div(7, 6)};
-  return t[s];
-}
-__host__ __device__ constexpr unsigned long long kCw24(int s) {
-  constexpr unsigned long long t[8] = {shell_cw_div(0, 24), shell_cw_div(1, 24), shell_cw_div(2, 24),
-                                       shell_cw_div(3, 24), shell_cw_div(4, 24), shell_cw_div(5, 24),
-                                       shell_cw_div(6, 24), shell_cw_div(7, 24)};
   return t[s];
 }
 

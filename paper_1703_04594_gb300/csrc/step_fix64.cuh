@@ -8,7 +8,7 @@
 //      (written back over its float64 in shared memory), checks the range of the
 //      fixed-point path and sums the moments in 64-bit fixed point;
 //   3. the site scalars in float64 (1/rho, u, T, gravity shift);
-//   4. the Hermite coefficients and, per shell, K0..K4 in fixed point; then a rolled loop
+//   4. the Hermite coefficients and, per shell, K0..K3 in fixed point; then a rolled loop
 //      over opposite pairs reads the fixed-point populations and evaluates the equilibrium
 //      polynomial and (1 - omega) f + omega f^eq.
 // Rolled loops keep the kernel's code small: the fully unrolled form of this arithmetic is
@@ -25,12 +25,12 @@ namespace d2q37 {
 
 struct ShellFix {
   long long cw, cq, cq2;
-  unsigned long long cw6, cw24;
+  unsigned long long cw6;
   int e;  // shell scale exponent e_s
   int lim;  // largest exponent field with |f| 2^e_s < 8
 };
 #define LBM_SHELL_FIX(s) \
-  { kCw(s), kCq(s), kCq2(s), kCw6(s), kCw24(s), shell_exp(s), 1025 - shell_exp(s) }
+  { kCw(s), kCq(s), kCq2(s), kCw6(s), shell_exp(s), 1025 - shell_exp(s) }
 static __constant__ ShellFix c_shell_fix[8] = {LBM_SHELL_FIX(0), LBM_SHELL_FIX(1), LBM_SHELL_FIX(2),
                                                LBM_SHELL_FIX(3), LBM_SHELL_FIX(4), LBM_SHELL_FIX(5),
                                                LBM_SHELL_FIX(6), LBM_SHELL_FIX(7)};
@@ -210,11 +210,12 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
       store(0, fx_to_double_dp(add_r(K0 + (NEG ? 0 : 1), fx_umulhi(om1u, sx[0])), 58 + e));
     }
     // K0 (58 bits) = w' (A00 + q A01 + q^2 A02), K1 (59) = w' (A10 + q A11),
-    // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, K4 (62) = omega rho w' / 24,
-    // formed at the first pair of each shell (pairs come grouped by shell).
+    // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, formed at the first pair of
+    // each shell (pairs come grouped by shell).  The s^4 / 24 term's factor
+    // omega rho w' s^2 / 24 is a quarter of K3 s^2 and takes no product of its own.
     int cur = -1, e = 0;
     long long K0 = 0, K1 = 0, K2 = 0;
-    unsigned long long K3 = 0, K4 = 0;
+    unsigned long long K3 = 0;
 #pragma unroll kFixUnrollRelax
     for (int j = 1; j <= NPAIR; ++j) {
       const PairFix pj = c_pair_fix[j];
@@ -226,16 +227,17 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
         K1 = fx_mulhi_su(A10, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 58 -> 59, 57 -> 59
         K2 = fx_mulhi_su(A20, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 59 -> 60, 58 -> 60
         K3 = fx_umulhi(Rf, c.cw6);
-        K4 = fx_umulhi(Rf, c.cw24) * 2;
         e = c.e;
       }
       const int vxk = pj.vx, vyk = pj.vy;
       const long long s = vxk * X1 + vyk * Y1;                                  // 63 bits, |s| < 0.6
       const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
       const long long s2 = (long long)fx_umulhi(as, as);                        // 62
-      const long long e1 = K2 + (long long)fx_umulhi(K4, (unsigned long long)s2);  // 60
+      // omega rho w' s^2 / 6 at 59 bits; halved, omega rho w' s^2 / 24 at 60 bits
+      const unsigned long long h3 = fx_umulhi(K3, (unsigned long long)s2);
+      const long long o1 = K1 + (long long)h3;                                   // 59
+      const long long e1 = K2 + (long long)(h3 >> 1);                            // 60
       const long long Ev = K0 + fx_mulhi_su(e1, (unsigned long long)s2);        // 58
-      const long long o1 = K1 + (long long)fx_umulhi(K3, (unsigned long long)s2);  // 59
       const long long Ov = fx_mulhi(o1, s);                                     // 58
       const unsigned long long rp = fx_umulhi(om1u, sx[j * 32]);                // 63 + 59 -> 58
       const unsigned long long rm = fx_umulhi(om1u, sx[(j + NPAIR) * 32]);
