@@ -156,10 +156,7 @@ __host__ __device__ constexpr int ghost_base(int i, int sign) {
 // (block 32 x 4 as the forward kernels).  `side` holds 2 * lx * kGhostSlots doubles: the
 // bottom slots of every column, then the top slots.
 template <bool PERIODIC>
-#ifndef LBM_ADJ_MIN_BLOCKS
-#define LBM_ADJ_MIN_BLOCKS 4
-#endif
-__global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const double* __restrict__ fin,
+__global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict__ fin,
                                                      const double* __restrict__ lam_next, double* __restrict__ lam_out,
                                                      double* __restrict__ side, double* __restrict__ dtau_part,
                                                      StepArgs a, double tau, double gx, double gy) {

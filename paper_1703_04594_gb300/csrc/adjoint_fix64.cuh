@@ -22,10 +22,6 @@
 #pragma once
 #include "collide_fix64.cuh"
 
-#ifndef LBM_ADJ_SHARED_H
-#define LBM_ADJ_SHARED_H 0
-#endif
-
 namespace d2q37 {
 
 // Per-shell constants: q = c^2 |v|^2 (59 fraction bits), q^2 (55), (q - D - 4)/4 (61),
@@ -139,14 +135,8 @@ __device__ __forceinline__ bool eq_vjp_sums_fix(double usx, double usy, double t
     const long long s = pk.vx * X1 + pk.vy * Y1;                                   // 63
     const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
     const unsigned long long s2 = fx_umulhi(as, as);                                // 62
-#if LBM_ADJ_SHARED_H
-    const unsigned long long h6u = fx_umulhi(s2, kInv6);                            // s^2/6, 62
-    const long long h6 = (long long)(h6u >> 3);                                     // s^2/6, 59
-    const long long h24 = (long long)(h6u >> 5);                                    // s^2/24, 59
-#else
     const long long h24 = (long long)(fx_umulhi(s2, kInv24) >> 3);                  // s^2/24, 59
     const long long h6 = (long long)(fx_umulhi(s2, kInv6) >> 3);                    // s^2/6, 59
-#endif
     const long long E = c0 + fx_mulhi_su(c2 + h24, s2) * 4;                          // 57 -> 59
     const long long O = fx_mulhi(c1 + h6, s) * 2;                                    // 58 -> 59
     const long long Pse = c1 + (long long)(s2 >> 4);                                 // + s^2/2
