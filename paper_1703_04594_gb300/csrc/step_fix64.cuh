@@ -4,16 +4,16 @@
 //   1. the 37 pull-gathered populations of the strip are copied global -> shared memory
 //      with cp.async (no registers held while the loads are in flight; inside a persistent
 //      kernel, whose sources were written earlier in the same launch, with L2 loads);
-//   2. a rolled loop over opposite pairs converts every population once to fixed point
+//   2. an unrolled loop over opposite pairs converts every population once to fixed point
 //      (written back over its float64 in shared memory), checks the range of the
 //      fixed-point path and sums the moments in 64-bit fixed point;
 //   3. the site scalars in float64 (1/rho, u, T, gravity shift);
-//   4. the Hermite coefficients and, per shell, K0..K3 in fixed point; then a rolled loop
-//      over opposite pairs reads the fixed-point populations and evaluates the equilibrium
-//      polynomial and (1 - omega) f + omega f^eq.
-// Rolled loops keep the kernel's code small: the fully unrolled form of this arithmetic is
-// ~8000 instructions per site, which thrashes the instruction cache.  Per-pair velocities
-// and shells, and per-shell constants, come from constant-memory tables.  Sites outside the
+//   4. the Hermite coefficients and, per shell, K0..K3 in fixed point; then a loop over
+//      opposite pairs (two per iteration) reads the fixed-point populations and evaluates
+//      the equilibrium polynomial and (1 - omega) f + omega f^eq.
+// The relaxation loop stays rolled to keep the kernel's code small (unrolled, it thrashes
+// the instruction cache); its per-pair velocities and shells, and per-shell constants,
+// come from constant-memory tables.  Sites outside the
 // fixed-point range take the float64 collision on their values loaded again from global
 // memory; warps next to a wall (two strips per column) run the float64 strip of
 // step_fp64.cuh.
@@ -63,21 +63,33 @@ __device__ __forceinline__ void cp_async8(double* smem_dst, const double* gmem_s
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Partial unrolling of the two pair loops (measured: 2 and 3 pairs per iteration give
-// +4 % over rolled loops; full unrolling overflows the instruction cache).
-#ifndef LBM_FIX64_UNROLL_MOMENTS
-#define LBM_FIX64_UNROLL_MOMENTS 2
-#endif
+// The moment loop is unrolled completely, with the pairs' velocities and shells as
+// compile-time constants; the relaxation loop takes 2 pairs per iteration from the
+// constant-memory tables (measured on GB300: +4 % and +2 % over 2 and 3 per iteration
+// from the tables; unrolling the relaxation loop completely overflows the instruction
+// cache and loses 11 %).
 #ifndef LBM_FIX64_UNROLL_RELAX
-#define LBM_FIX64_UNROLL_RELAX 3
+#define LBM_FIX64_UNROLL_RELAX 2
 #endif
-constexpr int kFixUnrollMoments = LBM_FIX64_UNROLL_MOMENTS;
 constexpr int kFixUnrollRelax = LBM_FIX64_UNROLL_RELAX;
 
 template <bool B>
 struct BoolConst {
   static constexpr bool value = B;
 };
+
+// Calls f(pair, j) for j = J .. NPAIR with the pair's data as compile-time constants: a
+// fully unrolled pair loop in which velocity multiples fold into adds.
+template <int J, class F>
+__device__ __forceinline__ void for_pairs_ct(F&& f) {
+  constexpr PairFix p = {rep_vx(J), rep_vy(J), rep_vx(J) * rep_vx(J) + rep_vy(J) * rep_vy(J), shell(J)};
+  f(p, J);
+  if constexpr (J < NPAIR) for_pairs_ct<J + 1>(f);
+}
+// Shell constants as compile-time values (for the unrolled loop).
+__device__ __forceinline__ constexpr ShellFix shell_ct(int s) {
+  return ShellFix{kCw(s), kCq(s), kCq2(s), kCw6(s), shell_exp(s), 1025 - shell_exp(s)};
+}
 
 // Shared staging: one warp holds sf[i * 32 + lane] for its 32 sites.
 constexpr int kFixWarps = 4;  // warps per block (block = 32 x 4 threads)
@@ -154,11 +166,9 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     sx[0] = q0;
     R = (q0 + (1LL << (2 + e))) >> (3 + e);
   }
-#pragma unroll kFixUnrollMoments
-  for (int k = 1; k <= NPAIR; ++k) {
-    const PairFix pk = c_pair_fix[k];
+  const auto moment_pair = [&](const PairFix pk, const int k) {
     const int vxk = pk.vx, vyk = pk.vy;
-    const ShellFix& c = c_shell_fix[pk.sh];
+    const ShellFix c = shell_ct(pk.sh);
     const double fa = sf[k * 32], fb = sf[(k + NPAIR) * 32];
     out |= ((unsigned long long)__double_as_longlong(fa) >> 52 > (unsigned)c.lim) |
            ((unsigned long long)__double_as_longlong(fb) >> 52 > (unsigned)c.lim);
@@ -173,7 +183,8 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     Ei += (long long)pk.v2 * P;
     Jx += (long long)vxk * M;
     Jy += (long long)vyk * M;
-  }
+  };
+  for_pairs_ct<1>(moment_pair);
   if (!active) return;
   const unsigned self = (unsigned)((long long)x * a.pitch + y);
   const auto store = [&](int i, double val) { __stcs(fout + i * a.pop + self, val); };
@@ -216,19 +227,14 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     int cur = -1, e = 0;
     long long K0 = 0, K1 = 0, K2 = 0;
     unsigned long long K3 = 0;
-#pragma unroll kFixUnrollRelax
-    for (int j = 1; j <= NPAIR; ++j) {
-      const PairFix pj = c_pair_fix[j];
-      const int sh = pj.sh;
-      if (sh != cur) {  // uniform across the warp
-        cur = sh;
-        const ShellFix& c = c_shell_fix[sh];
-        K0 = (fx_mulhi_su(A00, c.cw) + fx_mulhi_su(A01, c.cq) + fx_mulhi_su(A02, c.cq2)) * 2 + 3;
-        K1 = fx_mulhi_su(A10, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 58 -> 59, 57 -> 59
-        K2 = fx_mulhi_su(A20, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 59 -> 60, 58 -> 60
-        K3 = fx_umulhi(Rf, c.cw6);
-        e = c.e;
-      }
+    const auto shell_setup = [&](const ShellFix& c) {
+      K0 = (fx_mulhi_su(A00, c.cw) + fx_mulhi_su(A01, c.cq) + fx_mulhi_su(A02, c.cq2)) * 2 + 3;
+      K1 = fx_mulhi_su(A10, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 58 -> 59, 57 -> 59
+      K2 = fx_mulhi_su(A20, c.cw) * 2 + fx_mulhi_su(A11, c.cq) * 4 + 3;  // 59 -> 60, 58 -> 60
+      K3 = fx_umulhi(Rf, c.cw6);
+      e = c.e;
+    };
+    const auto pair_body = [&](const PairFix pj, const int j) {
       const int vxk = pj.vx, vyk = pj.vy;
       const long long s = vxk * X1 + vyk * Y1;                                  // 63 bits, |s| < 0.6
       const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
@@ -245,7 +251,16 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
       // and r enters with the sign of 1 - omega
       store(j, fx_to_double_dp(add_r(Ev + Ov + (NEG ? 1 : 2), rp), 58 + e));
       store(j + NPAIR, fx_to_double_dp(add_r(Ev - Ov + (NEG ? 0 : 1), rm), 58 + e));
-    }
+    };
+    const auto relax_pair = [&](const PairFix pj, const int j) {
+      if (pj.sh != cur) {  // uniform across the warp
+        cur = pj.sh;
+        shell_setup(c_shell_fix[pj.sh]);
+      }
+      pair_body(pj, j);
+    };
+#pragma unroll kFixUnrollRelax
+    for (int j = 1; j <= NPAIR; ++j) relax_pair(c_pair_fix[j], j);
   };
   if (a.cc.om1 < 0.0) relax(BoolConst<true>());
   else relax(BoolConst<false>());
