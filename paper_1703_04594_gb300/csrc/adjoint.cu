@@ -15,12 +15,12 @@
 //                                   + w [G_u . g + G_t (1 - 2 tau) |g|^2 / D];
 //      and the transpose of the pull is applied on the way out, as a push: out_i(z) is
 //      the value of lambda_i(z - v_i) when z - v_i is a fluid site.  When it is a ghost
-//      (z was fed from the wall), out_i(z) times the ghost's weight w_i P_i(T_wall) goes
-//      to a per-column slot of the wall's source column instead; entries lambda_i(x) with
-//      no fluid source x + v_i are set to zero by their own site;
+//      (z was fed from the wall), out_i(z) goes to a per-column slot of the wall's source
+//      column instead; entries lambda_i(x) with no fluid source x + v_i are set to zero
+//      by their own site;
 //   2. (k_adj_walls) the wall rows: every population of (x_s, 0) receives the sum of the
-//      bottom slots of column x_s (the transpose of rho_w = sum_j f_j(x_s, 0)), and
-//      likewise at the top.
+//      bottom slots of column x_s, each times its ghost's weight w_i P_i(T_wall) (the
+//      transpose of rho_w = sum_j f_j(x_s, 0)), and likewise at the top.
 // dL/dtau partials are summed per block and then in a fixed order (deterministic).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -203,17 +203,18 @@ __global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict
       const double om = 1.0 / tau, om1 = 1.0 - om;
       // out_i(z) is lambda_i(z - v_i) of the previous step (the transposed pull), or the
       // wall slot of its source column when z - v_i is a ghost
+      // (the destination is selected, not branched on, to keep the kernel's code small)
       const auto push = [&](int i, double val) {
         const int xs = wrap_index(x - vx(i), a.lx), yd = y - vy(i);
-        if (PERIODIC) {
-          __stcs(lam_out + i * a.pop + (long long)xs * a.pitch + wrap_index(yd, a.ly), val);
-        } else if (yd < 0) {
-          side[(long long)xs * kGhostSlots + ghost_base(i, 1) + y] = val * a.wall_b[i];
-        } else if (yd >= a.ly) {
-          side[((long long)a.lx + xs) * kGhostSlots + ghost_base(i, -1) + (a.ly - 1 - y)] = val * a.wall_t[i];
-        } else {
-          __stcs(lam_out + i * a.pop + (long long)xs * a.pitch + yd, val);
+        double* dst = lam_out + i * a.pop + (long long)xs * a.pitch + (PERIODIC ? wrap_index(yd, a.ly) : yd);
+        if (!PERIODIC && vy(i) > 0) {
+          double* g = side + (long long)xs * kGhostSlots + ghost_base(i, 1) + y;
+          dst = yd < 0 ? g : dst;
+        } else if (!PERIODIC && vy(i) < 0) {
+          double* g = side + ((long long)a.lx + xs) * kGhostSlots + ghost_base(i, -1) + (a.ly - 1 - y);
+          dst = yd >= a.ly ? g : dst;
         }
+        __stcs(dst, val);
       };
       // out_{+-v} = (1-w) mu + A_s +- B_v with A_s = w (nuR + nuE c^2 |v|^2) (one per shell)
       // and B_v = w c nuJ . v (from the multiples of w c nuJ)
@@ -244,9 +245,10 @@ __global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict
 }
 
 // Step 2: the wall rows' share of the transposed bc, after step 1 has written every
-// lambda entry: lambda_j(x, 0) += sum of the bottom slots of column x for all j (the ghost
-// values' dependence on rho_w(x) = sum_j f_j(x, 0)), and likewise for row ly - 1.  One
-// thread per column and wall (blockIdx.y: 0 bottom, 1 top).
+// lambda entry: lambda_j(x, 0) += sum over the bottom slots of column x of the slot's value
+// times its ghost's weight w_i P_i(T_bottom), for all j (the ghost values' dependence on
+// rho_w(x) = sum_j f_j(x, 0)), and likewise for row ly - 1.  One thread per column and
+// wall (blockIdx.y: 0 bottom, 1 top).
 __global__ void __launch_bounds__(128) k_adj_walls(const double* __restrict__ side, double* __restrict__ lam,
                                                    StepArgs a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,7 +257,16 @@ __global__ void __launch_bounds__(128) k_adj_walls(const double* __restrict__ si
   const double* src = side + ((long long)top * a.lx + x) * kGhostSlots;
   double wall = 0.0;
 #pragma unroll
-  for (int k = 0; k < kGhostSlots; ++k) wall += src[k];
+  for (int i = 0; i < Q; ++i) {  // rows in increasing y, then the ghost's weight
+    double t = 0.0;
+    if (top) {
+      for (int r = -vy(i) - 1; r >= 0; --r) t += src[ghost_base(i, -1) + r];
+      wall = vy(i) < 0 ? fma(t, a.wall_t[i], wall) : wall;
+    } else {
+      for (int r = 0; r < vy(i); ++r) t += src[ghost_base(i, 1) + r];
+      wall = vy(i) > 0 ? fma(t, a.wall_b[i], wall) : wall;
+    }
+  }
   double* dst = lam + (long long)x * a.pitch + (top ? a.ly - 1 : 0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) dst[i * a.pop] += wall;

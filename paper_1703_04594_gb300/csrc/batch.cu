@@ -136,16 +136,16 @@ __device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, l
 
 }  // namespace
 
-// Register caps: at most 256 threads per block (8 warps).  The FP32 step keeps three such
-// blocks resident per SM (<= 85 registers), the fixed-point FP64 step likewise (its shared
-// staging allows 6 blocks of 4 warps), the float64 step two (128 registers, as its
-// single-lattice kernel).
-constexpr int batch_min_blocks(int kind) { return kind == kFp64 ? 2 : 3; }
+// Register caps, with at most 256 threads per block (8 warps): the FP32 step keeps three
+// such blocks resident per SM (80 registers), the float64 step two (128 registers, as its
+// single-lattice kernel), the fixed-point FP64 step the 96 registers of its single-lattice
+// kernel (5 blocks of 4 warps per SM, which its shared staging also allows).
+constexpr int batch_max_regs(int kind) { return kind == kFp64 ? 128 : (kind == kFix64 ? 96 : 80); }
 
 extern __shared__ double batch_staged[];
 
 template <int KIND, bool PERIODIC>
-__global__ void __launch_bounds__(256, batch_min_blocks(KIND)) k_batch_step(const BatchLattice* __restrict__ L,
+__global__ void __launch_bounds__(256) __maxnreg__(batch_max_regs(KIND)) k_batch_step(const BatchLattice* __restrict__ L,
                                                     const unsigned short* __restrict__ tl, long long total,
                                                     int parity) {
   const long long t = blockIdx.x;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256, batch_min_blocks(KIND)) k_batch_step(cons
 }
 
 template <int KIND, bool PERIODIC>
-__global__ void __launch_bounds__(256, batch_min_blocks(KIND)) k_batch_persistent(const BatchLattice* __restrict__ L,
+__global__ void __launch_bounds__(256) __maxnreg__(batch_max_regs(KIND)) k_batch_persistent(const BatchLattice* __restrict__ L,
                                                           const unsigned short* __restrict__ tl, long long total,
                                                           int parity0, int steps, BatchSync* sync, unsigned phantom,
                                                           long long timeout_ns) {
