@@ -86,6 +86,27 @@ __host__ __device__ __forceinline__ unsigned long long fx_umulhi(unsigned long l
   return (unsigned long long)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
 #endif
 }
+// The high 64 bits of a b without the low partial product a0 b0 and without the carries
+// out of the low halves of the two cross products (a = a1 2^32 + a0, b = b1 2^32 + b0):
+// a1 b1 + hi(a1 b0) + hi(a0 b1), which is the floor of a b / 2^64 minus 0, 1 or 2
+// (about 3/4 on average for uniform operands: the floor of the sum of the two dropped
+// low halves and a0 b0 / 2^64).
+__host__ __device__ __forceinline__ unsigned long long fx_umulhi_approx(unsigned long long a, unsigned long long b) {
+  const unsigned a0 = (unsigned)a, a1 = (unsigned)(a >> 32), b0 = (unsigned)b, b1 = (unsigned)(b >> 32);
+  const unsigned h1 = (unsigned)(((unsigned long long)a1 * b0) >> 32);
+  const unsigned h2 = (unsigned)(((unsigned long long)a0 * b1) >> 32);
+  return (unsigned long long)a1 * b1 + h1 + h2;
+}
+__host__ __device__ __forceinline__ long long fx_mulhi_su_approx(long long a, unsigned long long b) {
+  const unsigned long long h = fx_umulhi_approx((unsigned long long)a, b);
+  return (long long)(a < 0 ? h - b : h);
+}
+__host__ __device__ __forceinline__ long long fx_mulhi_approx(long long a, long long b) {
+  unsigned long long h = fx_umulhi_approx((unsigned long long)a, (unsigned long long)b);
+  h -= a < 0 ? (unsigned long long)b : 0ull;
+  h -= b < 0 ? (unsigned long long)a : 0ull;
+  return (long long)h;
+}
 // Signed a times b with 0 <= b < 2^63: the unsigned product of a's bit pattern is
 // (a + 2^64) b when a < 0, whose high half exceeds that of a b by exactly b.
 __host__ __device__ __forceinline__ long long fx_mulhi_su(long long a, unsigned long long b) {

@@ -73,6 +73,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 #endif
 constexpr int kFixUnrollRelax = LBM_FIX64_UNROLL_RELAX;
 
+
 template <bool B>
 struct BoolConst {
   static constexpr bool value = B;
@@ -238,19 +239,24 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
       const int vxk = pj.vx, vyk = pj.vy;
       const long long s = vxk * X1 + vyk * Y1;                                  // 63 bits, |s| < 0.6
       const unsigned long long as = (unsigned long long)(s < 0 ? -s : s);
-      const long long s2 = (long long)fx_umulhi(as, as);                        // 62
+      // The products drop the low partial product and the carries of the low halves
+      // (fx_umulhi_approx): 0 to 2 units below the floor of the exact high half, about
+      // 1.25 below the exact product on average, far inside the outputs' 5 guard bits.
+      const long long s2 = (long long)fx_umulhi_approx(as, as);                 // 62
       // omega rho w' s^2 / 6 at 59 bits; halved, omega rho w' s^2 / 24 at 60 bits
-      const unsigned long long h3 = fx_umulhi(K3, (unsigned long long)s2);
+      const unsigned long long h3 = fx_umulhi_approx(K3, (unsigned long long)s2);
       const long long o1 = K1 + (long long)h3;                                   // 59
       const long long e1 = K2 + (long long)(h3 >> 1);                            // 60
-      const long long Ev = K0 + fx_mulhi_su(e1, (unsigned long long)s2);        // 58
-      const long long Ov = fx_mulhi(o1, s);                                     // 58
-      const unsigned long long rp = fx_umulhi(om1u, sx[j * 32]);                // 63 + 59 -> 58
-      const unsigned long long rm = fx_umulhi(om1u, sx[(j + NPAIR) * 32]);
-      // re-centring: Ev, Ov and r each come out of a truncation 1/2 unit low on average,
-      // and r enters with the sign of 1 - omega
-      store(j, fx_to_double_dp(add_r(Ev + Ov + (NEG ? 1 : 2), rp), 58 + e));
-      store(j + NPAIR, fx_to_double_dp(add_r(Ev - Ov + (NEG ? 0 : 1), rm), 58 + e));
+      const long long Ev = K0 + fx_mulhi_su_approx(e1, (unsigned long long)s2); // 58
+      const long long Ov = fx_mulhi_approx(o1, s);                              // 58
+      const unsigned long long rp = fx_umulhi_approx(om1u, sx[j * 32]);         // 63 + 59 -> 58
+      const unsigned long long rm = fx_umulhi_approx(om1u, sx[(j + NPAIR) * 32]);
+      // re-centring: Ev, Ov and r each come out about 1.25 units low on average (r only
+      // 1/2 when 1 - omega has at most 32 significant bits), and r enters with the sign
+      // of 1 - omega; the offsets keep each output within about a unit of its exact value
+      // on average (the mass-drift tests bound the effect).
+      store(j, fx_to_double_dp(add_r(Ev + Ov + (NEG ? 2 : 4), rp), 58 + e));
+      store(j + NPAIR, fx_to_double_dp(add_r(Ev - Ov + (NEG ? -1 : 1), rm), 58 + e));
     };
     const auto relax_pair = [&](const PairFix pj, const int j) {
       if (pj.sh != cur) {  // uniform across the warp

@@ -5,6 +5,9 @@
 //   mulsu <a decimal> <b decimal>   -> fx_mulhi_su(a, b)
 //   mul <a decimal> <b decimal>     -> fx_mulhi(a, b)
 //   umul <a decimal> <b decimal>    -> fx_umulhi(a, b)
+//   uapx <a decimal> <b decimal>    -> fx_umulhi_approx(a, b)
+//   sapx <a decimal> <b decimal>    -> fx_mulhi_approx(a, b)
+//   suapx <a decimal> <b decimal>   -> fx_mulhi_su_approx(a, b)
 //   const                           -> the shell constants, one shell per line
 #include <cstdio>
 #include <cstring>
@@ -47,6 +50,19 @@ int main() {
       unsigned long long a, b;
       std::scanf("%llu %llu", &a, &b);
       std::printf("%llu\n", fx_umulhi(a, b));
+    } else if (!std::strcmp(cmd, "uapx")) {
+      unsigned long long a, b;
+      std::scanf("%llu %llu", &a, &b);
+      std::printf("%llu\n", fx_umulhi_approx(a, b));
+    } else if (!std::strcmp(cmd, "sapx")) {
+      long long a, b;
+      std::scanf("%lld %lld", &a, &b);
+      std::printf("%lld\n", fx_mulhi_approx(a, b));
+    } else if (!std::strcmp(cmd, "suapx")) {
+      long long a;
+      unsigned long long b;
+      std::scanf("%lld %llu", &a, &b);
+      std::printf("%lld\n", fx_mulhi_su_approx(a, b));
     } else if (!std::strcmp(cmd, "const")) {
       for (int s = 0; s < 8; ++s)
         std::printf("%d %d %lld %lld %lld %llu\n", s, shell_exp(s), kCw(s), kCq(s), kCq2(s), kCw6(s));

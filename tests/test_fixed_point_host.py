@@ -124,3 +124,27 @@ def test_products_keep_the_floor_of_the_high_half(probe):
     want = [(a * b) >> 64 for a, b in su + ss + uu]                # Python >> floors
     assert [int(x) for x in out] == want
 
+
+
+def test_approximate_products_are_0_to_2_below_the_floor(probe):
+    """The relaxation loop's products drop the low partial product and the carries of the
+    low halves: the result is floor(a b / 2^64) minus 0, 1 or 2.  For random operands the
+    deficit is the floor of U1 + U2 + U3 with U1, U2 uniform on [0, 1) and U3 the product of
+    two such: 3/4 on average (the re-centring offsets rest on that mean)."""
+    rng = random.Random(13)
+    lim = 1 << 63
+    m32 = (1 << 32) - 1
+    uu = [((1 << 64) - 1, (1 << 64) - 1), (m32, m32), ((m32 << 32) | m32, 1 << 32), (0, 5), (1 << 63, 3)]
+    ss = [(-(1 << 63), -(1 << 63)), (-1, -1), ((1 << 63) - 1, -(1 << 63)), (-3, 5)]
+    su = [(-1, 1), (-(1 << 63), (1 << 63) - 1), (-5, 7), (0, 12345)]
+    for _ in range(2000):
+        uu.append((rng.randrange(0, 1 << 64), rng.randrange(0, 1 << 64)))
+        ss.append((rng.randrange(-lim, lim), rng.randrange(-lim, lim)))
+        su.append((rng.randrange(-lim, lim), rng.randrange(0, lim)))
+    out = probe([f"uapx {a} {b}" for a, b in uu] + [f"sapx {a} {b}" for a, b in ss] +
+                [f"suapx {a} {b}" for a, b in su])
+    got = [int(x) for x in out]
+    deficits = [((a * b) >> 64) - g for (a, b), g in zip(uu + ss + su, got)]
+    assert all(d in (0, 1, 2) for d in deficits)
+    rand = deficits[5:2005]                                       # the random unsigned cases
+    assert abs(sum(rand) / len(rand) - 0.75) < 0.05
