@@ -71,6 +71,16 @@ __device__ __forceinline__ double fx_to_double_dp(long long X, int k) {
   return X == 0 ? 0.0 : __longlong_as_double(b);
 }
 
+// The same for 0 <= k <= 1022 without a test for zero: the I2F result's high word h is 0
+// for X = 0 and at least 0x3FF00000 otherwise (|X| >= 1; a sign bit makes it larger
+// still), so subtracting min(h, k << 20) leaves 0 at 0 and lowers the exponent field of
+// every other value by k.
+__device__ __forceinline__ double fx_to_double_dp_pos(long long X, int k) {
+  const double d = __ll2double_rn(X);
+  const unsigned h = (unsigned)__double2hiint(d), K = (unsigned)k << 20;
+  return __hiloint2double((int)(h - min(h, K)), __double2loint(d));
+}
+
 // High 64 bits of the 128-bit products.
 __host__ __device__ __forceinline__ long long fx_mulhi(long long a, long long b) {
 #ifdef __CUDA_ARCH__

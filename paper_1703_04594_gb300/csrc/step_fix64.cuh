@@ -74,6 +74,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr int kFixUnrollRelax = LBM_FIX64_UNROLL_RELAX;
 
 
+
 template <bool B>
 struct BoolConst {
   static constexpr bool value = B;
@@ -191,8 +192,8 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   const auto store = [&](int i, double val) { __stcs(fout + i * a.pop + self, val); };
   // 3. site scalars in float64; sites out of range (negative or large populations, fast or
   //    hot fluid) take the float64 collision
-  const SiteScalars v = scalars_from_moments(fx_to_double_dp(R, 56), fx_to_double_dp(Jx, 56),
-                                             fx_to_double_dp(Jy, 56), fx_to_double_dp(Ei, 56), a.cc);
+  const SiteScalars v = scalars_from_moments(fx_to_double_dp_pos(R, 56), fx_to_double_dp_pos(Jx, 56),
+                                             fx_to_double_dp_pos(Jy, 56), fx_to_double_dp_pos(Ei, 56), a.cc);
   if (out || !fixed_range_ok(v)) {
     collide_site_reloaded<PERIODIC, Ld>(fin, fout, a, x, yc, self);
     return;
@@ -219,7 +220,7 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     {
       constexpr int e = shell_exp(0);
       const long long K0 = fx_mulhi_su(A00, kCw(0)) * 2 + 1;
-      store(0, fx_to_double_dp(add_r(K0 + (NEG ? 0 : 1), fx_umulhi(om1u, sx[0])), 58 + e));
+      store(0, fx_to_double_dp_pos(add_r(K0 + (NEG ? 0 : 1), fx_umulhi(om1u, sx[0])), 58 + e));
     }
     // K0 (58 bits) = w' (A00 + q A01 + q^2 A02), K1 (59) = w' (A10 + q A11),
     // K2 (60) = w' (A20 + q A21), K3 (61) = omega rho w' / 6, formed at the first pair of
@@ -255,8 +256,8 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
       // 1/2 when 1 - omega has at most 32 significant bits), and r enters with the sign
       // of 1 - omega; the offsets keep each output within about a unit of its exact value
       // on average (the mass-drift tests bound the effect).
-      store(j, fx_to_double_dp(add_r(Ev + Ov + (NEG ? 2 : 4), rp), 58 + e));
-      store(j + NPAIR, fx_to_double_dp(add_r(Ev - Ov + (NEG ? -1 : 1), rm), 58 + e));
+      store(j, fx_to_double_dp_pos(add_r(Ev + Ov + (NEG ? 2 : 4), rp), 58 + e));
+      store(j + NPAIR, fx_to_double_dp_pos(add_r(Ev - Ov + (NEG ? -1 : 1), rm), 58 + e));
     };
     const auto relax_pair = [&](const PairFix pj, const int j) {
       if (pj.sh != cur) {  // uniform across the warp
