@@ -22,7 +22,7 @@
 // re-centred by small constant offsets to within half a unit of 2^-58, far below the
 // systematic error that the float64 weights themselves put on mass conservation.
 //
-// Range.  The path is taken for sites with 0 <= f_i 2^e_s < 8 for all i,
+// Range.  The path is taken for sites with 2^-7 <= f_i 2^e_s < 8 for all i,
 // 0 < omega rho < 3, |c u_s,x| and |c u_s,y| below 0.15 (so |s| < 0.6) and
 // |T_s - 1| < 0.25; then every intermediate stays inside its format.  All other sites (and
 // NaNs) take the float64 collision of collide_site, so results never depend on the range.

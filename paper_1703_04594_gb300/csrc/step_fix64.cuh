@@ -36,24 +36,20 @@ static __constant__ ShellFix c_shell_fix[8] = {LBM_SHELL_FIX(0), LBM_SHELL_FIX(1
                                                LBM_SHELL_FIX(6), LBM_SHELL_FIX(7)};
 #undef LBM_SHELL_FIX
 
-// x >> r with PTX semantics: shift amounts of 64 or more give 0.
-__device__ __forceinline__ unsigned long long shr_clamped(unsigned long long x, unsigned r) {
-  unsigned long long y;
-  asm("shr.b64 %0, %1, %2;" : "=l"(y) : "l"(x), "r"(r));
-  return y;
+// f' = f 2^(59 + e) for a population whose value is an integer there: with the exponent
+// field E, sh = E - 1016 + e is the left shift of the 53-bit significand, and
+// 2^-7 <= f 2^e < 8 is 0 <= sh <= 9 (one unsigned compare, which also fails for negative
+// values, zeros, subnormals and non-finite ones).  fx_exact_shift returns whether f is in
+// that range; fx_from_double_shifted forms the integer with two funnel shifts.
+__device__ __forceinline__ bool fx_exact_shift(double f, int e, unsigned& sh) {
+  sh = ((unsigned)__double2hiint(f) >> 20) + (unsigned)e - 1016u;
+  return sh <= 9u;
 }
-
-// round(v 2^k) for a float64 v >= 0 with v 2^k < 2^62 (callers guarantee both); integer
-// instructions only, round half up.  With the significand m (implicit bit included),
-// v 2^k = m 2^sh; the value is formed with one extra fraction bit,
-// m 2^(sh + 1) = (m 2^11) >> (10 - sh), where m 2^11 is the bit pattern shifted left by 11
-// with the implicit bit set.  Zeros, subnormals and values below half a unit give 0 (their
-// shift is 64 or more).
-__device__ __forceinline__ long long fx_from_nonneg(double v, int k) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned E = (unsigned)(b >> 52);  // sign bit clear
-  const unsigned long long x = (b << 11) | 0x8000000000000000ull;
-  return (long long)((shr_clamped(x, 1085u - E - (unsigned)k) + 1) >> 1);
+__device__ __forceinline__ long long fx_from_double_shifted(double f, unsigned sh) {
+  const unsigned lo = (unsigned)__double2loint(f);
+  const unsigned mh = ((unsigned)__double2hiint(f) & 0xFFFFFu) | 0x100000u;
+  const unsigned xh = __funnelshift_l(lo, mh, sh), xl = lo << sh;
+  return (long long)(((unsigned long long)xh << 32) | xl);
 }
 
 // 8-byte asynchronous global -> shared copy (sm_80+ LDGSTS), cached in L1.
@@ -156,15 +152,18 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   long long* const sx = reinterpret_cast<long long*>(sf);  // the same slots, as fixed point
   // 2. every population to fixed point f' = f 2^(59 + e_s), written back in place, and the
   //    moments from f' rounded to 2^-56: rho, j and sum |v|^2 f stay below 2^4 there for
-  //    every state in range.  The exponent field of a population in range is at most
-  //    1025 - e_s; a negative one has the sign bit set, so one unsigned compare flags both.
+  //    every state in range.  In range, 2^-7 <= f 2^e_s < 8, f 2^(59 + e_s) is an integer
+  //    (its significand shifted left by 0 to 9 places), so the conversion is exact; one
+  //    unsigned compare of the exponent field flags everything else (negative, zero,
+  //    small, large, non-finite), and such a site takes the float64 collision.
   bool out;
   long long R, Ei = 0, Jx = 0, Jy = 0;
   {
     constexpr int e = shell_exp(0);
     const double f0 = sf[0];
-    out = (unsigned long long)__double_as_longlong(f0) >> 52 > 1025 - e;
-    const long long q0 = fx_from_nonneg(f0, 59 + e);
+    unsigned sh0;
+    out = !fx_exact_shift(f0, e, sh0);
+    const long long q0 = fx_from_double_shifted(f0, sh0);
     sx[0] = q0;
     R = (q0 + (1LL << (2 + e))) >> (3 + e);
   }
@@ -172,9 +171,9 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
     const int vxk = pk.vx, vyk = pk.vy;
     const ShellFix c = shell_ct(pk.sh);
     const double fa = sf[k * 32], fb = sf[(k + NPAIR) * 32];
-    out |= ((unsigned long long)__double_as_longlong(fa) >> 52 > (unsigned)c.lim) |
-           ((unsigned long long)__double_as_longlong(fb) >> 52 > (unsigned)c.lim);
-    const long long qa = fx_from_nonneg(fa, 59 + c.e), qb = fx_from_nonneg(fb, 59 + c.e);
+    unsigned sha, shb;
+    out |= !fx_exact_shift(fa, c.e, sha) | !fx_exact_shift(fb, c.e, shb);
+    const long long qa = fx_from_double_shifted(fa, sha), qb = fx_from_double_shifted(fb, shb);
     sx[k * 32] = qa;
     sx[(k + NPAIR) * 32] = qb;
     const int sh = 3 + c.e;
@@ -190,8 +189,8 @@ __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin,
   if (!active) return;
   const unsigned self = (unsigned)((long long)x * a.pitch + y);
   const auto store = [&](int i, double val) { __stcs(fout + i * a.pop + self, val); };
-  // 3. site scalars in float64; sites out of range (negative or large populations, fast or
-  //    hot fluid) take the float64 collision
+  // 3. site scalars in float64; sites out of range (populations outside [2^-7, 8) 2^-e_s,
+  //    fast or hot fluid) take the float64 collision
   const SiteScalars v = scalars_from_moments(fx_to_double_dp_pos(R, 56), fx_to_double_dp_pos(Jx, 56),
                                              fx_to_double_dp_pos(Jy, 56), fx_to_double_dp_pos(Ei, 56), a.cc);
   if (out || !fixed_range_ok(v)) {

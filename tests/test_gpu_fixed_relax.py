@@ -71,15 +71,39 @@ def moving_fields(p, ux, uy, temp):
 
 
 @pytest.mark.parametrize("ux,uy,temp", [
-    (0.14, -0.12, 1.2),    # inside the range, near its edge: |c u| ~ 0.17-0.18, T_s - 1 ~ 0.22
+    (0.11, -0.10, 1.2),    # inside the range, near its edge: |c u_x| up to 0.145, T_s - 1 up to 0.22
     (0.30, 0.05, 1.0),     # too fast: every site takes the float64 relaxation
     (0.02, 0.01, 1.45),    # too hot: float64 relaxation
-    (0.16, 0.0, 1.0),      # straddles the edge |c u_x| = 0.2: mixed warps
+    (0.125, 0.0, 1.0),     # |c u_x| from 0.135 to 0.165 straddles the edge 0.15: mixed warps
 ])
 def test_range_edges_and_fallback(ux, uy, temp):
     p = lbm.Params(48, 64, tau=0.9, gy=-1e-4, bc=lbm.BC_PERIODIC_Y, precision=lbm.FP64_FIXED)
     fields = moving_fields(p, ux, uy, torch.full((p.lx, p.ly), temp, dtype=torch.float64))
     assert rel_err(to_host(p, run_fixed(p, fields, 5)), oracle_run(p, fields, 5)) <= STEP_TOL
+
+
+def test_tiny_and_zero_populations_take_the_float64_relaxation():
+    """A population outside [2^-7, 8) times its shell scale 2^-e_s (here 0 and 1e-12 in two
+    shells) puts its site outside the fixed-point range: that site takes the float64
+    relaxation, so its outputs agree with the float64 step's to rounding (the same
+    arithmetic), and every output stays within the parity bar of the oracle."""
+    fx = lbm.Params(40, 64, tau=0.8, gy=-1e-4, precision=lbm.FP64_FIXED)
+    fd = lbm.Params(40, 64, tau=0.8, gy=-1e-4)
+    _, _, vx, vy = lbm.model()
+    f = device_init(fx, rt_fields(fx, seed=21))
+    hit = torch.zeros(fx.lx, fx.ly, dtype=torch.bool)
+    for i, val, xs, ys in ((36, 0.0, slice(0, None, 3), slice(5, 60, 7)),
+                           (30, 1e-12, slice(1, None, 3), slice(4, 60, 5))):
+        f[i, xs, ys] = val
+        src = torch.zeros(fx.lx, fx.ly, dtype=torch.bool)
+        src[xs, ys] = True
+        hit |= torch.roll(src, shifts=(vx[i], vy[i]), dims=(0, 1))    # where it is pulled to
+    host = to_host(fx, f)
+    a = to_host(fx, lbm.step(fx, f, lbm.empty_state(fx)))
+    b = to_host(fd, lbm.step(fd, f, lbm.empty_state(fd)))
+    assert int(hit.sum()) > 50
+    assert rel_err(a[:, hit], b[:, hit]) <= 1e-15
+    assert rel_err(a, OL.step(host, oracle_params(fx))) <= STEP_TOL
 
 
 def test_fixed_and_float64_relaxations_agree_on_a_long_run():
