@@ -41,7 +41,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture
 # of the current kernel on a smaller lattice, scaled to 4096 x 8192 by the site count;
 # profiles/ holds the captures).  None where no capture of the current kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = {"fused": 18.13e9, "separate": None, "fp32": 9.16e9, "fp64fix": 19.20e9}
+TRAFFIC_BYTES_PER_LAUNCH = {"fused": 18.13e9, "separate": None, "fp32": 9.16e9, "fp64fix": 19.10e9}
 
 
 def _hbm_peak():
