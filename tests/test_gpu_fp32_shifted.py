@@ -72,6 +72,19 @@ def test_hundred_steps_vs_oracle():
     check(field_errors(got, want))
 
 
+def test_512x1024_1000_steps_vs_fp64_gpu():
+    """The precision workload's crop size: 512 x 1024, seed 2, 1000 steps.  The oracle would
+    need about an hour of host cores for it, so the FP64 GPU path (pinned to the oracle at
+    1e-12 by the FP64 parity tests) is the reference here."""
+    p64 = lbm.Params(512, 1024)
+    p32 = fp32(p64)
+    fields = rt_fields(p64, seed=2)
+    r64 = lbm.run(p64, device_init(p64, fields), lbm.empty_state(p64), 1000)
+    m64 = [t.clone() for t in lbm.moments(p64, r64)]
+    r32 = lbm.run(p32, device_init(p32, fields), lbm.empty_state(p32), 1000)
+    check(field_errors(lbm.moments(p32, r32), m64))
+
+
 def test_full_size_1000_steps_vs_fp64_gpu():
     """4096 x 8192, seed 2, 1000 steps: FP32 shifted storage against the FP64 GPU path
     (itself pinned to the oracle by the FP64 parity tests)."""
