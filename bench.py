@@ -288,6 +288,28 @@ def run_ours(a):
                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                     "hbm_gbs_equiv": BYTES_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e9}
 
+    # end to end through the C-ABI from pinned host fields: H2D, init, K steps, moments, D2H
+    pinned_in = [t.contiguous().pin_memory() for t in fields]
+    pinned_out = [torch.empty(lx, ly, dtype=torch.float64).pin_memory() for _ in range(4)]
+    fdev = torch.empty(4 * sites, dtype=torch.float64, device="cuda")
+    lbm.simulate_host(p, pinned_in, 1, pinned_out, fa, fb, fdev, stream)
+    runs = []
+    with ClockSampler(local) as eclk:
+        for _ in range(3):                    # median of three end-to-end runs
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            lbm.simulate_host(p, pinned_in, a.steps, pinned_out, fa, fb, fdev, stream)
+            runs.append(max_over_ranks(time.perf_counter() - t0, "cuda"))
+    e2e_s = statistics.median(runs)
+    field_bytes = 4 * sites * 8
+    e2e = {"value": whole_job_mlups(sites, a.steps, world, e2e_s * 1e3), "unit": "MLUPS",
+           "h2d_bytes_per_step": field_bytes / a.steps, "d2h_bytes_per_step": field_bytes / a.steps,
+           "what": "lbm_simulate_host: fields H2D + init + K steps + moments + fields D2H, amortised per "
+                   "step; median of 3 calls",
+           "runs_s": runs, "clocks": eclk.summary()}
+    del pinned_in, pinned_out, fdev
+
     # the same FP64 step with the fixed-point relaxation (LBM_FP64_FIXED), on the same lattice
     fixed_line = None
     if a.precision == "fp64" and a.variant == "fused" and not a.no_fixed:
@@ -334,27 +356,6 @@ def run_ours(a):
         prop_line = {"kernel": "k_propagate_push_fp64" if a.variant == "push" else "k_propagate_fp64",
                      "ms": prop_ms, "bytes": prop_bytes, "achieved": gbs, "unit": "GB/s",
                      "frac": gbs / HBM_PEAK_GBS, "peak": HBM_PEAK_GBS}
-
-    # end to end through the C-ABI from pinned host fields: H2D, init, K steps, moments, D2H
-    pinned_in = [t.contiguous().pin_memory() for t in fields]
-    pinned_out = [torch.empty(lx, ly, dtype=torch.float64).pin_memory() for _ in range(4)]
-    fdev = torch.empty(4 * sites, dtype=torch.float64, device="cuda")
-    del dev
-    lbm.simulate_host(p, pinned_in, 1, pinned_out, fa, fb, fdev, stream)
-    runs = []
-    for _ in range(3):                        # median of three end-to-end runs
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        lbm.simulate_host(p, pinned_in, a.steps, pinned_out, fa, fb, fdev, stream)
-        runs.append(max_over_ranks(time.perf_counter() - t0, "cuda"))
-    e2e_s = statistics.median(runs)
-    field_bytes = 4 * sites * 8
-    e2e = {"value": whole_job_mlups(sites, a.steps, world, e2e_s * 1e3), "unit": "MLUPS",
-           "h2d_bytes_per_step": field_bytes / a.steps, "d2h_bytes_per_step": field_bytes / a.steps,
-           "what": "lbm_simulate_host: fields H2D + init + K steps + moments + fields D2H, amortised per "
-                   "step; median of 3 calls",
-           "runs_s": runs}
 
     if rank == 0:
         line = {"metric": "D2Q37 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
