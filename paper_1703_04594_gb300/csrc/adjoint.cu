@@ -206,15 +206,18 @@ __global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict
       // (the destination is selected, not branched on, to keep the kernel's code small)
       const auto push = [&](int i, double val) {
         const int xs = wrap_index(x - vx(i), a.lx), yd = y - vy(i);
-        double* dst = lam_out + i * a.pop + (long long)xs * a.pitch + (PERIODIC ? wrap_index(yd, a.ly) : yd);
+        const long long in_fluid = i * a.pop + (long long)xs * a.pitch + (PERIODIC ? wrap_index(yd, a.ly) : yd);
+        bool ghost = false;
+        long long slot = 0;
         if (!PERIODIC && vy(i) > 0) {
-          double* g = side + (long long)xs * kGhostSlots + ghost_base(i, 1) + y;
-          dst = yd < 0 ? g : dst;
+          ghost = yd < 0;
+          slot = (long long)xs * kGhostSlots + ghost_base(i, 1) + y;
         } else if (!PERIODIC && vy(i) < 0) {
-          double* g = side + ((long long)a.lx + xs) * kGhostSlots + ghost_base(i, -1) + (a.ly - 1 - y);
-          dst = yd >= a.ly ? g : dst;
+          ghost = yd >= a.ly;
+          slot = ((long long)a.lx + xs) * kGhostSlots + ghost_base(i, -1) + (a.ly - 1 - y);
         }
-        __stcs(dst, val);
+        // only the selected address is formed (the other offset may be out of its buffer)
+        __stcs(ghost ? side + slot : lam_out + in_fluid, val);
       };
       // out_{+-v} = (1-w) mu + A_s +- B_v with A_s = w (nuR + nuE c^2 |v|^2) (one per shell)
       // and B_v = w c nuJ . v (from the multiples of w c nuJ)

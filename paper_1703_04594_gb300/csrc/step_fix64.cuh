@@ -48,7 +48,7 @@ __device__ __forceinline__ bool fx_exact_shift(double f, int e, unsigned& sh) {
 __device__ __forceinline__ long long fx_from_double_shifted(double f, unsigned sh) {
   const unsigned lo = (unsigned)__double2loint(f);
   const unsigned mh = ((unsigned)__double2hiint(f) & 0xFFFFFu) | 0x100000u;
-  const unsigned xh = __funnelshift_l(lo, mh, sh), xl = lo << sh;
+  const unsigned xh = __funnelshift_l(lo, mh, sh), xl = lo << (sh & 31u);  // sh <= 9 in range
   return (long long)(((unsigned long long)xh << 32) | xl);
 }
 
