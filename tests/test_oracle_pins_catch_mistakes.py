@@ -82,3 +82,69 @@ def test_wrong_wall_density_row_is_caught(monkeypatch):
         return orig(f_tilde, torch.roll(f_prev, 1, dims=2), p)   # density from the wrong row
     monkeypatch.setattr(L, "bc", bad_bc)
     assert _fails(TS.test_bc_ghost_values_hand_computed)
+
+
+def test_relaxation_with_tau_instead_of_its_inverse_is_caught(monkeypatch):
+    def bad_collide(f_tilde, p):
+        rho, u, T = L.moments(f_tilde)
+        u_s, T_s = L.gravity_shift(u, T, p)
+        return f_tilde - (f_tilde - M.equilibrium(rho, u_s, T_s)) * p.tau
+    monkeypatch.setattr(L, "collide", bad_collide)
+    assert _fails(TS.test_collide_relaxation_is_linear_blend)
+
+
+def test_temperature_without_the_dimension_factor_is_caught(monkeypatch):
+    orig = L.moments
+
+    def bad_moments(f):
+        rho, u, T = orig(f)
+        return rho, u, T * M.D
+    monkeypatch.setattr(L, "moments", bad_moments)
+    assert _fails(TS.test_moments_recover_equilibrium_fields)
+
+
+def test_swapped_wall_temperatures_are_caught(monkeypatch):
+    orig = L.bc
+
+    def bad_bc(f_tilde, f_prev, p):
+        q = L.Params(p.lx, p.ly, tau=p.tau, gx=p.gx, gy=p.gy, t_bottom=p.t_top, t_top=p.t_bottom, bc=p.bc)
+        return orig(f_tilde, f_prev, q)
+    monkeypatch.setattr(L, "bc", bad_bc)
+    assert _fails(TS.test_bc_ghost_values_hand_computed)
+
+
+def test_gravity_with_the_wrong_sign_is_caught(monkeypatch):
+    orig = L.gravity_shift
+
+    def bad_shift(u, T, p):
+        q = L.Params(p.lx, p.ly, tau=p.tau, gx=-p.gx, gy=-p.gy, t_bottom=p.t_bottom, t_top=p.t_top, bc=p.bc)
+        return orig(u, T, q)
+    monkeypatch.setattr(L, "gravity_shift", bad_shift)
+    assert _fails(TS.test_collide_gravity_kick_and_unchanged_temperature)
+
+
+def test_missing_periodic_wrap_in_x_is_caught(monkeypatch):
+    def clamped(f, p):
+        q, lx, ly = f.shape
+        out = torch.empty_like(f)
+        for i in range(q):
+            vx, vy = M.VELOCITIES[i]
+            xs = (torch.arange(lx) - vx).clamp(0, lx - 1)
+            ys = torch.arange(ly) - vy
+            ys = ys % ly if p.bc == "periodic_y" else ys.clamp(0, ly - 1)
+            out[i] = f[i][xs][:, ys]
+        return out
+    monkeypatch.setattr(L, "propagate", clamped)
+    assert _fails(TS.test_propagate_brute_force_indices, "walls")
+
+
+@pytest.mark.parametrize("mutation", ["swap_shell_weights", "scale_off_by_1e-3"])
+def test_wrong_weights_or_lattice_scale_are_caught(monkeypatch, mutation):
+    if mutation == "swap_shell_weights":
+        w = M.W_SHELL[:]
+        w[6], w[7] = w[7], w[6]
+        monkeypatch.setattr(M, "WEIGHTS", torch.tensor([w[s] for s in M.SHELL_INDEX], dtype=torch.float64))
+    else:
+        monkeypatch.setattr(M, "XI", M.XI * 1.001)
+    pq = [(p, q) for p in range(9) for q in range(9) if p + q <= 9]
+    assert any(_fails(TM.test_lattice_isotropy_all_moments_to_order_eight, p, q) for p, q in pq)
