@@ -75,10 +75,22 @@ __device__ __forceinline__ double fx_to_double_dp(long long X, int k) {
 // for X = 0 and at least 0x3FF00000 otherwise (|X| >= 1; a sign bit makes it larger
 // still), so subtracting min(h, k << 20) leaves 0 at 0 and lowers the exponent field of
 // every other value by k.
-__device__ __forceinline__ double fx_to_double_dp_pos(long long X, int k) {
+// (The host build, for the tests, converts with the host's round-to-nearest cast.)
+__host__ __device__ __forceinline__ double fx_to_double_dp_pos(long long X, int k) {
+#ifdef __CUDA_ARCH__
   const double d = __ll2double_rn(X);
   const unsigned h = (unsigned)__double2hiint(d), K = (unsigned)k << 20;
   return __hiloint2double((int)(h - min(h, K)), __double2loint(d));
+#else
+  const double d = (double)X;
+  unsigned long long b;
+  __builtin_memcpy(&b, &d, 8);
+  const unsigned h = (unsigned)(b >> 32), K = (unsigned)k << 20;
+  b = ((unsigned long long)(h - (h < K ? h : K)) << 32) | (b & 0xFFFFFFFFull);
+  double r;
+  __builtin_memcpy(&r, &b, 8);
+  return r;
+#endif
 }
 
 // High 64 bits of the 128-bit products.

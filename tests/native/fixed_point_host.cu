@@ -2,6 +2,7 @@
 // tests: reads commands from stdin and prints results, one per line.
 //   from <v as hex bits> <k>        -> fx_from_double(v, k) (decimal)
 //   to <X decimal> <k>              -> fx_to_double(X, k) (hex bits)
+//   top <X decimal> <k>             -> fx_to_double_dp_pos(X, k) (hex bits)
 //   mulsu <a decimal> <b decimal>   -> fx_mulhi_su(a, b)
 //   mul <a decimal> <b decimal>     -> fx_mulhi(a, b)
 //   umul <a decimal> <b decimal>    -> fx_umulhi(a, b)
@@ -34,6 +35,14 @@ int main() {
       int k;
       std::scanf("%lld %d", &X, &k);
       const double d = fx_to_double(X, k);
+      unsigned long long bits;
+      std::memcpy(&bits, &d, 8);
+      std::printf("%016llx\n", bits);
+    } else if (!std::strcmp(cmd, "top")) {
+      long long X;
+      int k;
+      std::scanf("%lld %d", &X, &k);
+      const double d = fx_to_double_dp_pos(X, k);
       unsigned long long bits;
       std::memcpy(&bits, &d, 8);
       std::printf("%016llx\n", bits);

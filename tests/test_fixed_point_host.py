@@ -148,3 +148,18 @@ def test_approximate_products_are_0_to_2_below_the_floor(probe):
     assert all(d in (0, 1, 2) for d in deficits)
     rand = deficits[5:2005]                                       # the random unsigned cases
     assert abs(sum(rand) / len(rand) - 0.75) < 0.05
+
+
+def test_exponent_lowering_conversion_keeps_zero_and_rounds_to_nearest(probe):
+    """fx_to_double_dp_pos: X 2^-k as the round-to-nearest float64 of X with its exponent
+    lowered by k, and 0 for X = 0 (no test for zero: the unsigned min on the exponent
+    word), for the kernels' formats k = 56 and 58 + e_s (60..69) and signed X."""
+    rng = random.Random(17)
+    cases = [(0, 56), (0, 69), (1, 60), (-1, 60), ((1 << 63) - 1, 69), (-(1 << 63), 58), (3, 56)]
+    for _ in range(500):
+        X = rng.randint(1, (1 << rng.randint(1, 63)) - 1) * rng.choice([-1, 1])
+        cases.append((X, rng.choice([56, 60, 61, 62, 64, 65, 66, 67, 69])))
+    out = probe([f"top {X} {k}" for X, k in cases])
+    for (X, k), got in zip(cases, out):
+        want = 0.0 if X == 0 else float(X) * 2.0 ** -k      # float(X) rounds to nearest
+        assert from_bits(got) == want and bits(from_bits(got)) == bits(want), (X, k)
