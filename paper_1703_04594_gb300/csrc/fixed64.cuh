@@ -93,6 +93,45 @@ __host__ __device__ __forceinline__ double fx_to_double_dp_pos(long long X, int 
 #endif
 }
 
+// f' = f 2^(59 + e) for a population whose value is an integer there: with the exponent
+// field E, sh = E - 1016 + e is the left shift of the 53-bit significand, and
+// 2^-7 <= f 2^e < 8 is 0 <= sh <= 9 (one unsigned compare, which also fails for negative
+// values, zeros, subnormals and non-finite ones).  fx_exact_shift returns whether f is in
+// that range; fx_from_double_shifted forms the integer with two funnel shifts.
+__host__ __device__ __forceinline__ unsigned fx_hi_word(double f) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2hiint(f);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &f, 8);
+  return (unsigned)(b >> 32);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned fx_lo_word(double f) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2loint(f);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &f, 8);
+  return (unsigned)b;
+#endif
+}
+__host__ __device__ __forceinline__ bool fx_exact_shift(double f, int e, unsigned& sh) {
+  sh = (fx_hi_word(f) >> 20) + (unsigned)e - 1016u;
+  return sh <= 9u;
+}
+__host__ __device__ __forceinline__ long long fx_from_double_shifted(double f, unsigned sh) {
+  const unsigned lo = fx_lo_word(f);
+  const unsigned mh = (fx_hi_word(f) & 0xFFFFFu) | 0x100000u;
+#ifdef __CUDA_ARCH__
+  const unsigned xh = __funnelshift_l(lo, mh, sh);
+#else
+  const unsigned xh = (unsigned)((((unsigned long long)mh << 32) | lo) << (sh & 31u) >> 32);
+#endif
+  const unsigned xl = lo << (sh & 31u);  // sh <= 9 in range
+  return (long long)(((unsigned long long)xh << 32) | xl);
+}
+
 // High 64 bits of the 128-bit products.
 __host__ __device__ __forceinline__ long long fx_mulhi(long long a, long long b) {
 #ifdef __CUDA_ARCH__

@@ -36,22 +36,6 @@ static __constant__ ShellFix c_shell_fix[8] = {LBM_SHELL_FIX(0), LBM_SHELL_FIX(1
                                                LBM_SHELL_FIX(6), LBM_SHELL_FIX(7)};
 #undef LBM_SHELL_FIX
 
-// f' = f 2^(59 + e) for a population whose value is an integer there: with the exponent
-// field E, sh = E - 1016 + e is the left shift of the 53-bit significand, and
-// 2^-7 <= f 2^e < 8 is 0 <= sh <= 9 (one unsigned compare, which also fails for negative
-// values, zeros, subnormals and non-finite ones).  fx_exact_shift returns whether f is in
-// that range; fx_from_double_shifted forms the integer with two funnel shifts.
-__device__ __forceinline__ bool fx_exact_shift(double f, int e, unsigned& sh) {
-  sh = ((unsigned)__double2hiint(f) >> 20) + (unsigned)e - 1016u;
-  return sh <= 9u;
-}
-__device__ __forceinline__ long long fx_from_double_shifted(double f, unsigned sh) {
-  const unsigned lo = (unsigned)__double2loint(f);
-  const unsigned mh = ((unsigned)__double2hiint(f) & 0xFFFFFu) | 0x100000u;
-  const unsigned xh = __funnelshift_l(lo, mh, sh), xl = lo << (sh & 31u);  // sh <= 9 in range
-  return (long long)(((unsigned long long)xh << 32) | xl);
-}
-
 // 8-byte asynchronous global -> shared copy (sm_80+ LDGSTS), cached in L1.
 __device__ __forceinline__ void cp_async8(double* smem_dst, const double* gmem_src) {
   const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);

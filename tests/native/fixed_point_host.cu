@@ -3,6 +3,7 @@
 //   from <v as hex bits> <k>        -> fx_from_double(v, k) (decimal)
 //   to <X decimal> <k>              -> fx_to_double(X, k) (hex bits)
 //   top <X decimal> <k>             -> fx_to_double_dp_pos(X, k) (hex bits)
+//   exact <v as hex bits> <e>       -> in-range flag and fx_from_double_shifted (decimal)
 //   mulsu <a decimal> <b decimal>   -> fx_mulhi_su(a, b)
 //   mul <a decimal> <b decimal>     -> fx_mulhi(a, b)
 //   umul <a decimal> <b decimal>    -> fx_umulhi(a, b)
@@ -46,6 +47,15 @@ int main() {
       unsigned long long bits;
       std::memcpy(&bits, &d, 8);
       std::printf("%016llx\n", bits);
+    } else if (!std::strcmp(cmd, "exact")) {
+      unsigned long long bits;
+      int e;
+      std::scanf("%llx %d", &bits, &e);
+      double v;
+      std::memcpy(&v, &bits, 8);
+      unsigned sh;
+      const bool ok = fx_exact_shift(v, e, sh);
+      std::printf("%d %lld\n", ok ? 1 : 0, ok ? fx_from_double_shifted(v, sh) : 0LL);
     } else if (!std::strcmp(cmd, "mulsu")) {
       long long a;
       unsigned long long b;

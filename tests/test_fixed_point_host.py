@@ -163,3 +163,25 @@ def test_exponent_lowering_conversion_keeps_zero_and_rounds_to_nearest(probe):
     for (X, k), got in zip(cases, out):
         want = 0.0 if X == 0 else float(X) * 2.0 ** -k      # float(X) rounds to nearest
         assert from_bits(got) == want and bits(from_bits(got)) == bits(want), (X, k)
+
+
+def test_exact_input_conversion_and_its_range(probe):
+    """fx_exact_shift / fx_from_double_shifted: a population f with 2^-7 <= f 2^e < 8 is
+    flagged in range and converted to exactly f 2^(59 + e) (an integer there); zero,
+    negative, tiny, large and non-finite values are flagged out of range."""
+    rng = random.Random(19)
+    cases = []
+    for e in (2, 3, 4, 6, 7, 9, 11):
+        for v in (2.0 ** -7, 8.0 - 2.0 ** -50, 1.0, 0.5 + 2.0 ** -52):
+            cases.append((v * 2.0 ** -e, e))
+        for v in (0.0, -0.0, -1.0, 8.0, 2.0 ** -7 - 2.0 ** -60, 1e-300, 5e-324, float("inf"), float("nan")):
+            cases.append((v * 2.0 ** -e if v == v and abs(v) != float("inf") else v, e))
+        for _ in range(100):
+            cases.append((rng.uniform(0.0, 9.0) * 2.0 ** (-e - rng.choice([0, 0, 0, 4, 8])), e))
+    out = probe([f"exact {bits(v)} {e}" for v, e in cases])
+    for (v, e), line in zip(cases, out):
+        flag, q = (int(x) for x in line.split())
+        inside = v == v and Fraction(1, 128) <= Fraction(v) * 2 ** e < 8 if v == v and abs(v) != float("inf") else False
+        assert flag == int(inside), (v, e)
+        if inside:
+            assert Fraction(q) == Fraction(v) * 2 ** (59 + e), (v, e)
