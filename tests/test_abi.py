@@ -86,6 +86,26 @@ def test_invalid_params_rejected(lib, bad):
     assert st == lbm.EINVAL
 
 
+@pytest.mark.parametrize("lx,ly,ok", [
+    (4 * 65535, 6, True),          # the largest lx the launch grid takes (grid.y = lx / 4)
+    (4 * 65535 + 1, 6, False),
+    (65535, 65504, True),          # one population plane just below 2^32 elements
+    (65536, 65536, False),         # a plane of exactly 2^32 elements
+    (131072, 32768, False),
+])
+def test_maximum_sizes(lib, lx, ly, ok):
+    """Sizes at the edge of what the 32-bit in-plane offsets and the launch grid allow are
+    accepted or rejected by the parameter check alone (no launch, nothing allocated)."""
+    p = lbm.Params(lx, ly)
+    pitch = lib.lbm_pitch(ctypes.byref(p.c()))
+    if ok:
+        assert pitch == (ly + 31) // 32 * 32 and lx * pitch < 2 ** 32
+    else:
+        assert pitch == -1
+        st = lib.lbm_step(ctypes.byref(p.c()), ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 40), None)
+        assert st == lbm.EINVAL
+
+
 def test_aliasing_and_alignment_rejected(lib):
     p = lbm.Params(8, 8)
     nbytes = lbm.buffer_bytes(p)
