@@ -13,10 +13,9 @@
 //      the equilibrium polynomial and (1 - omega) f + omega f^eq.
 // The relaxation loop stays rolled to keep the kernel's code small (unrolled, it thrashes
 // the instruction cache); its per-pair velocities and shells, and per-shell constants,
-// come from constant-memory tables.  Sites outside the
-// fixed-point range take the float64 collision on their values loaded again from global
-// memory; warps next to a wall (two strips per column) run the float64 strip of
-// step_fp64.cuh.
+// come from constant-memory tables.  Sites outside the fixed-point range take the float64
+// collision on their values loaded again from global memory; warps next to a wall (two
+// strips per column) run the float64 strip of step_fp64.cuh.
 #pragma once
 #include "collide_fix64.cuh"
 #include "step_fp64.cuh"
@@ -27,7 +26,7 @@ struct ShellFix {
   long long cw, cq, cq2;
   unsigned long long cw6;
   int e;  // shell scale exponent e_s
-  int lim;  // largest exponent field with |f| 2^e_s < 8
+  int lim;  // largest exponent field with |f| 2^e_s < 8 (the range is checked by fx_exact_shift)
 };
 #define LBM_SHELL_FIX(s) \
   { kCw(s), kCq(s), kCq2(s), kCw6(s), shell_exp(s), 1025 - shell_exp(s) }
@@ -52,8 +51,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 #define LBM_FIX64_UNROLL_RELAX 2
 #endif
 constexpr int kFixUnrollRelax = LBM_FIX64_UNROLL_RELAX;
-
-
 
 template <bool B>
 struct BoolConst {
