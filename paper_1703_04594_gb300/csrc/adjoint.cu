@@ -150,13 +150,30 @@ __host__ __device__ constexpr int ghost_base(int i, int sign) {
   return sign > 0 ? b[i] : t[i];
 }
 
+// The pull-gather of a warp's strip into its shared-memory slots sf[i * 32 + lane] through
+// registers (wall bc and periodic wrap included); not inlined, so that its 37 live values
+// do not weigh on the register allocation of the collide kernel.
+template <bool PERIODIC>
+__device__ __noinline__ void gather_to_shared(const double* __restrict__ fin, const StepArgs& a, int x, int y0,
+                                              int yc, double* sf) {
+  double f[Q];
+  gather_strip_fp64<PERIODIC>(fin, a, a, x, y0, yc, f, LdReadOnly());
+#pragma unroll
+  for (int i = 0; i < Q; ++i) sf[i * 32] = f[i];
+}
+
+__device__ __forceinline__ void cp_async8_adj(double* smem_dst, const double* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+
 }  // namespace
 
 // Step 1: per-site adjoint of the collision with the transposed propagate as its store
 // (block 32 x 4 as the forward kernels).  `side` holds 2 * lx * kGhostSlots doubles: the
 // bottom slots of every column, then the top slots.
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict__ fin,
+__global__ void __launch_bounds__(128, 5) k_adj_collide(const double* __restrict__ fin,
                                                      const double* __restrict__ lam_next, double* __restrict__ lam_out,
                                                      double* __restrict__ side, double* __restrict__ dtau_part,
                                                      StepArgs a, double tau, double gx, double gy) {
@@ -167,11 +184,25 @@ __global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict
   if (x < a.lx) {  // uniform per warp
     const bool active = y < a.ly;
     const int yc = active ? y : a.ly - 1;
-    double f[Q];
-    gather_strip_fp64<PERIODIC>(fin, a, a, x, y0, yc, f, LdReadOnly());
+    // the strip's pull-gather staged in shared memory (9.5 KB per warp): no registers held
+    // for it, which lets 5 blocks of 4 warps share an SM (389 against 399 us per step with
+    // the gather in registers at 4 blocks)
+    __shared__ double staged[4][Q * 32];
+    double* const sf = &staged[threadIdx.y][0] + (threadIdx.x & 31);
+    if (PERIODIC || y0 < 3 || y0 + 32 > a.ly - 3) {
+      gather_to_shared<PERIODIC>(fin, a, x, y0, yc, sf);
+    } else {
+      unsigned off[7];  // column x_s, row yc within a population plane
+#pragma unroll
+      for (int d = 0; d < 7; ++d) off[d] = (unsigned)((long long)wrap_index(x - (d - 3), a.lx) * a.pitch + yc);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) cp_async8_adj(sf + i * 32, fin + i * a.pop + (off[vx(i) + 3] - vy(i)));
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+    const auto fget = [&](int i) { return sf[i * 32]; };
     if (active) {
       double rho, jx, jy, e;
-      moments_int(f, rho, jx, jy, e);
+      moments_get(fget, rho, jx, jy, e, [](int, int) {});
       const double inv = 1.0 / rho;
       const double Jx = C * jx, Jy = C * jy, E = C2 * e;  // xi-unit moments
       const double ux = Jx * inv, uy = Jy * inv;
@@ -184,7 +215,7 @@ __global__ void __launch_bounds__(128, 4) k_adj_collide(const double* __restrict
       const double* lam = lam_next + o;
       double mu_ft = 0.0;  // sum_i mu_i f~_i
 #pragma unroll
-      for (int i = 0; i < Q; ++i) mu_ft = fma(__ldg(lam + i * a.pop), f[i], mu_ft);
+      for (int i = 0; i < Q; ++i) mu_ft = fma(__ldg(lam + i * a.pop), fget(i), mu_ft);
       // the VJP in fixed point (adjoint_fix64.cuh), in float64 outside its range
       EqVjp G;
       VjpSums V;
