@@ -213,3 +213,18 @@ def test_fixed_point_moment_sums_within_float64_summation_error():
             exact = math.fsum(g[:, x, y].tolist())
             worst = max(worst, abs(float(rho[x, y]) - exact))
     assert worst <= 37 * 2.0 ** -53 + 2.3e-16, worst
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP64_FIXED])
+def test_stored_oracle_fixture(precision):
+    """The GPU steps against the stored oracle fixture tests/golden/rt_16x32_3steps.txt
+    (16 x 32, seed 9, 3 steps): per-population sums and three sampled sites."""
+    from tests.test_golden_fixture import load_golden, maker
+    SITES = maker().SITES
+    p = lbm.Params(16, 32, precision=precision)
+    res = to_host(p, lbm.run(p, device_init(p, rt_fields(p, seed=9)), lbm.empty_state(p), 3))
+    want = load_golden()
+    for i in range(37):
+        got = [float(res[i].sum())] + [float(res[i, x, y]) for x, y in SITES]
+        for a, b in zip(got, want[i]):
+            assert abs(a - b) <= STEP_TOL * abs(b), (i, a, b)
