@@ -1,5 +1,6 @@
-"""bench.py's clock record, on the CPU: the summary of nvidia-smi samples taken during a
-timed region (median SM clock under load, maximum clock, throttle reasons)."""
+"""bench.py's measurement bookkeeping, on the CPU: the summary of nvidia-smi samples taken
+during a timed region (median SM clock under load, maximum clock, throttle reasons) and
+the source of the HBM peak (the measured file, else the stated fallback)."""
 import importlib.util
 import os
 
@@ -38,3 +39,13 @@ def test_throttle_reasons_are_reported():
 def test_unsampled_when_nvidia_smi_gave_nothing():
     s = summary_of(["", "garbage line"])
     assert s["sm_mhz"] is None and s["reasons"] == ["unsampled"]
+
+
+def test_hbm_peak_from_the_measured_file_else_the_fallback(tmp_path):
+    b = bench_module()
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6774.6, "bf16_tflops": 1900}')
+    assert b._hbm_peak(str(tmp_path)) == (6774.6, "MEASURED_PEAKS.json hbm_gbs (of measured)")
+    empty = tmp_path / "none"
+    empty.mkdir()
+    peak, source = b._hbm_peak(str(empty))
+    assert peak == 6800.0 and "fallback" in source
