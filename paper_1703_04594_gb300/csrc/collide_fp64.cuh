@@ -66,11 +66,13 @@ __device__ __forceinline__ void moments_get(Fget&& fget, double& rho, double& jx
   int E0, Ea, Eb;
   long long R = to_fix52_e(fget(0), E0), Ei = 0, Jx = 0, Jy = 0;
   on_exp(0, E0);
+  int emax = E0;
 #pragma unroll
   for (int k = 1; k <= NPAIR; ++k) {
     const long long a = to_fix52_e(fget(k), Ea), b = to_fix52_e(fget(k + NPAIR), Eb);
     on_exp(k, Ea);
     on_exp(k + NPAIR, Eb);
+    emax = max(emax, max(Ea, Eb));
     const long long P = a + b, M = a - b;
     R += P;
     Ei += (long long)v2(k) * P;
@@ -82,6 +84,10 @@ __device__ __forceinline__ void moments_get(Fget&& fget, double& rho, double& jx
   e = (double)Ei * S;
   jx = (double)Jx * S;
   jy = (double)Jy * S;
+  // a population of magnitude 2^11 or more (an infinity, a NaN, or far outside any
+  // physical state) has no fixed-point form: the moments become NaN, so the site's
+  // outputs are NaN too, as a float64 sum would make them
+  if (emax > 1033) rho = e = jx = jy = __longlong_as_double(0x7FF8000000000000LL);
 }
 
 __device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, double& jx, double& jy, double& e) {

@@ -163,3 +163,29 @@ def test_full_size_sampled_columns():
     del res, got
     torch.cuda.empty_cache()
 
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP64_FIXED])
+def test_injected_nan_reaches_exactly_its_destination_site(precision):
+    """Fault made on the host: one population of one site is set to NaN.  After one step
+    the site it is pulled to, and only that site, holds NaN in every population (its
+    moments are NaN, so lbm_moments flags it); every other site is unchanged with respect
+    to a clean run.  Both the float64 and the fixed-point forms (whose range check sends
+    the site to the float64 collision) behave the same way."""
+    p = lbm.Params(24, 48, precision=precision)
+    _, _, vx, vy = lbm.model()
+    fields = rt_fields(p, seed=23)
+    clean = device_init(p, fields)
+    bad = clean.clone()
+    i, xs, ys = 30, 5, 20
+    bad[i, xs, ys] = float("nan")
+    a = to_host(p, lbm.step(p, clean, lbm.empty_state(p)))
+    b = to_host(p, lbm.step(p, bad, lbm.empty_state(p)))
+    xd, yd = (xs + vx[i]) % p.lx, ys + vy[i]
+    nan_sites = torch.isnan(b).any(dim=0)
+    assert nan_sites.sum() == 1 and bool(nan_sites[xd, yd])
+    assert bool(torch.isnan(b[:, xd, yd]).all())
+    keep = ~nan_sites
+    assert torch.equal(a[:, keep], b[:, keep])
+    rho = lbm.moments(p, lbm.step(p, bad, lbm.empty_state(p)))[0].cpu()
+    assert torch.isnan(rho).sum() == 1 and bool(torch.isnan(rho[xd, yd]))
