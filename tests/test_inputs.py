@@ -54,3 +54,17 @@ def test_fields_differentiable_in_amplitudes():
     rho, _, _, T = I.rt_fields(lx, ly, m)
     (rho.sum() + T.sum()).backward()
     assert m.a.grad is not None and torch.isfinite(m.a.grad).all()
+
+
+def test_batch_workload_follows_its_recipe():
+    """The batched workload: 256 lattices, Lx from {128, 192, ..., 1024}, Ly = 2 Lx,
+    tau in [0.6, 1.0], distinct interface seeds, deterministic for its seed, and the
+    234.0 M sites the batched bench line reports for seed 4."""
+    w = I.batch_workload()
+    assert w == I.batch_workload() and len(w) == 256
+    assert all(lx in range(128, 1025, 64) and ly == 2 * lx for lx, ly, _, _ in w)
+    assert all(0.6 <= tau <= 1.0 for _, _, tau, _ in w)
+    assert len({s for *_, s in w}) == 256
+    assert len({lx for lx, *_ in w}) >= 12            # uneven sizes: most of the 15 values occur
+    assert round(sum(lx * ly for lx, ly, _, _ in w) / 1e6, 1) == 234.0
+    assert I.batch_workload(seed=5) != w
