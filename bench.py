@@ -40,8 +40,10 @@ BYTES_PER_SITE_FP32 = 296          # 37 x 4 B read + 37 x 4 B written
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture
 # of the current kernel on a smaller lattice, scaled to 4096 x 8192 by the site count;
-# profiles/ holds the captures).  None where no capture of the current kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = {"fused": 18.13e9, "separate": None, "fp32": 9.16e9, "fp64fix": 19.10e9}
+# profiles/ holds the captures).  None where no capture of the current kernel exists: the
+# float64 and fixed-point steps gained the moments' range check (integer instructions, the
+# same memory accesses) after their captures (18.13 GB and 19.10 GB per launch then).
+TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None, "fp32": 9.16e9, "fp64fix": None}
 
 
 def _hbm_peak(root=None):
