@@ -7,6 +7,7 @@ import os
 import re
 
 import pytest
+import torch
 
 from paper_1703_04594_gb300 import lbm
 
@@ -114,3 +115,20 @@ def test_aliasing_and_alignment_rejected(lib):
     assert lib.lbm_step(ctypes.byref(p.c()), ctypes.c_void_p(base + 8), ctypes.c_void_p(base + 4 * nbytes), None) == lbm.EINVAL
     assert lib.lbm_run(ctypes.byref(p.c()), ctypes.c_void_p(base), ctypes.c_void_p(base + 4 * nbytes), -1, None) == lbm.EINVAL
     assert lib.lbm_strerror(lbm.EINVAL).startswith(b"invalid")
+
+
+def test_binding_rejects_host_tensors_and_wrong_buffers_before_any_call(lib):
+    """The Python binding checks device, dtype, contiguity and size of every state and
+    field argument before it calls into the library (so these run without a GPU)."""
+    p = lbm.Params(8, 8)
+    n = lbm.buffer_bytes(p) // 8
+    host_state = torch.zeros(n, dtype=torch.float64)
+    with pytest.raises(ValueError, match="f_in"):
+        lbm.step(p, host_state, host_state)
+    with pytest.raises(ValueError, match="f_in"):
+        lbm.step(p, torch.zeros(n, dtype=torch.float32), host_state)
+    p32 = lbm.Params(8, 8, precision=lbm.FP32_SHIFTED)
+    assert lbm.state_dtype(p32) == torch.float32 and lbm.buffer_bytes(p32) == lbm.buffer_bytes(p) // 2
+    field = torch.zeros(8, 8, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        lbm.init(p, field, field, field, field, host_state)
