@@ -8,11 +8,22 @@ shape).  One bench step = one fused propagate + bc + collide pass over the whole
 lattice (one kernel launch).  Each state buffer is 9.9 GB, far larger than the 129 MB
 L2, so no L2 flush is needed between steps.
 
+The default line also carries the other forms of the step, each with its own roofline,
+clock samples and baseline: ``fp64_fixed_relax`` (float64 states, fixed-point relaxation),
+``fp32`` (FP32 shifted storage, same lattice), ``batch_fp64`` / ``batch_fp32`` (256
+independent RT lattices, Lx in 128..1024, Ly = 2 Lx, K steps, against looping the
+single-lattice kernel) and ``adjoint`` (gradient of the kinetic energy after 500 steps of a
+512 x 1024 lattice with checkpoints every 22 steps, against the forward run, and the
+adjoint step kernel against its HBM roofline).
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--variant fused|separate|push|aos|psoa|caosoa]
+    python bench.py --workload batch --steps 200 [--precision fp32|fp64|fp64fix] [--batch-kind small]
+    python bench.py --workload adjoint
     python bench.py --impl reference      # the float64 CPU oracle on a bounded sample
 
 Under torchrun (N > 1) every rank steps its own replica lattice (independent problems:
-weak scaling, no collective on the data path); rank 0 prints one JSON line.
+weak scaling, no collective on the data path); rank 0 prints one JSON line with the
+headline forms only.
 """
 from __future__ import annotations
 
@@ -30,20 +41,22 @@ sys.path.insert(0, ROOT)
 LX, LY, SEED = 4096, 8192, 2
 TAU, GY, T_BOTTOM, T_TOP = 0.8, -1e-4, 1.15, 0.85
 
-# Algorithmic work per site of the fused FP64 step (counted from the factored
-# formulation in csrc/collide_fp64.cuh; FMA = 2 flops):
-#   138 add + 97 mul + 138 fma + 1 div = 512 flops, 374 FP64-pipe operations.
+# Algorithmic work per site of the fused FP64 step: the factored collision (moments as
+# pair sums grouped by their integer velocity weights, per-shell Hermite coefficients, one
+# even/odd Horner pair per opposite pair, BGK relaxation), FMA = 2 flops:
+#   138 add + 97 mul + 138 fma + 1 div = 512 flops, 374 operations.
+# tests/test_flop_count.py counts it mechanically on a formulation checked against the
+# oracle's collision.
+FLOP_MIX_FP64 = (138, 97, 138, 1)      # add, mul, fma, div
 FLOPS_PER_SITE_FP64 = 512
 BYTES_PER_SITE_FP64 = 592          # 37 x 8 B read + 37 x 8 B written
 BYTES_PER_SITE_FP32 = 296          # 37 x 4 B read + 37 x 4 B written
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture
-# of the current kernel on a smaller lattice, scaled to 4096 x 8192 by the site count;
-# profiles/ holds the captures).  None where no capture of the current kernel exists: the
-# float64 and fixed-point steps gained the moments' range check (integer instructions, the
-# same memory accesses) after their captures (18.13 GB and 19.10 GB per launch then).
-TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None, "fp32": 9.16e9, "fp64fix": None}
+# of the current kernel on a smaller lattice, scaled to the bench's lattice by the site
+# count; profiles/ holds the captures).  None where no capture of the current kernel exists.
+TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None, "fp32": None, "fp64fix": None, "adjoint": None}
 
 
 def _hbm_peak(root=None):
@@ -74,6 +87,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed", action="store_true",
                     help="skip the extra timing of the fixed-point-relaxation FP64 step")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32, batched and adjoint forms that the default line adds")
+    ap.add_argument("--batch-kind", choices=["uneven", "small"], default="uneven",
+                    help="uneven = 256 lattices, Lx in 128..1024, Ly = 2 Lx; small = 1024 lattices, "
+                         "Lx in 32..128 (a launch-bound batch)")
     ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
                     help="batch = 256 independent lattices of uneven sizes; adjoint = gradient of the "
                          "kinetic energy after 500 steps of a 512x1024 lattice (checkpoints every 22)")
@@ -220,8 +238,9 @@ def run_ours(a):
     p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
                    precision=lbm.FP32_SHIFTED if fp32 else (lbm.FP64_FIXED if fix else lbm.FP64))
     sites = lx * ly
-    fields = I.rt_state(lx, ly, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))
-    dev = [t.contiguous().cuda() for t in fields]
+    dev = [t.contiguous() for t in I.rt_state(lx, ly, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY),
+                                              device="cuda")]
+    fields = [t.cpu() for t in dev]
     fa, fb = lbm.empty_state(p), lbm.empty_state(p)
     separate = a.variant in ("separate", "push")
     ftmp = lbm.empty_state(p) if separate else None
@@ -360,6 +379,20 @@ def run_ours(a):
                      "ms": prop_ms, "bytes": prop_bytes, "achieved": gbs, "unit": "GB/s",
                      "frac": gbs / HBM_PEAK_GBS, "peak": HBM_PEAK_GBS}
 
+    # the other forms of the step, each with its own roofline, clocks and baseline (one GPU:
+    # they are per-GPU forms; the replicas of N > 1 report the headline only)
+    forms = {}
+    if (world == 1 and a.precision == "fp64" and a.variant == "fused" and not a.no_forms
+            and (lx, ly) == (LX, LY)):
+        del bufs, fa, fb, ftmp
+        torch.cuda.empty_cache()
+        forms["fp32"] = single_form(a, "fp32", dev)
+        del dev
+        torch.cuda.empty_cache()
+        forms["batch_fp64"] = batch_form(a, "fp64")
+        forms["batch_fp32"] = batch_form(a, "fp32")
+        forms["adjoint"] = adjoint_form(a, repeats=3)
+
     if rank == 0:
         line = {"metric": "D2Q37 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -376,6 +409,7 @@ def run_ours(a):
                 "roofline": roofline, "e2e": e2e,
                 **({"propagate_kernel": prop_line} if prop_line else {}),
                 **({"fp64_fixed_relax": fixed_line} if fixed_line else {}),
+                **forms,
                 "gpu_launches": a.steps * (3 if separate else 1),
                 "clocks": clk.summary()}
         if not a.no_cpu_baseline and world == 1 and (lx, ly) == (LX, LY):
@@ -385,102 +419,237 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def run_batch(a):
-    """Batched form: independent RT lattices (Lx in 128..1024 step 64 drawn by seed 4,
-    Ly = 2 Lx, tau ~ U[0.6, 1.0], own interface seeds) stepped by one persistent launch
-    (autotuned), against looping the single-lattice kernel over the lattices."""
+def kernel_roofline(bound, work_per_site, sites, ms, kernel, traffic=None):
+    """Roofline record of one kernel: algorithmic bytes (hbm) or flops (alu) per launch over
+    its CUDA-event time, against the measured HBM copy rate or the FP64 unit-count peak."""
+    if bound == "hbm":
+        achieved = work_per_site * sites / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": achieved / HBM_PEAK_GBS, "traffic": traffic, "kernel": kernel,
+                "peak_source": HBM_PEAK_SOURCE}
+    achieved = work_per_site * sites / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel,
+            "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+
+
+def single_form(a, precision, dev_fields):
+    """One 4096 x 8192 lattice in another storage form (fp32 = FP32 shifted deviations):
+    K steps timed with CUDA events, against its HBM roofline."""
+    import torch
+
+    from paper_1703_04594_gb300 import lbm
+
+    p = lbm.Params(LX, LY, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
+                   precision={"fp32": lbm.FP32_SHIFTED, "fp64fix": lbm.FP64_FIXED}[precision])
+    bufs = [lbm.empty_state(p), lbm.empty_state(p)]
+    lbm.init(p, *dev_fields, bufs[0])
+    stream = torch.cuda.current_stream()
+    for k in range(a.warmup):
+        lbm.step(p, bufs[k % 2], bufs[(k + 1) % 2], stream)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(0) as clk:
+        ev[0].record(stream)
+        for k in range(a.steps):
+            lbm.step(p, bufs[(a.warmup + k) % 2], bufs[(a.warmup + k + 1) % 2], stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / a.steps
+    sites = LX * LY
+    fp32 = precision == "fp32"
+    out = {"value": sites / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": a.steps,
+           "dtype": "f32+i64+f64" if fp32 else "f64+i64",
+           "workload": f"{LX}x{LY} RT lattice, seed {SEED}",
+           "roofline": kernel_roofline("hbm", BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64, sites, ms,
+                                       "k_step_fp32" if fp32 else "k_step_fix64",
+                                       TRAFFIC_BYTES_PER_LAUNCH.get(precision)),
+           "gpu_launches": a.steps, "clocks": clk.summary()}
+    del bufs
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_lattices(kind, n, seed):
+    """(lx, ly, tau, interface seed) of every lattice of a batched workload."""
+    from paper_1703_04594_gb300 import inputs as I
+
+    if kind == "small":
+        return I.batch_workload(seed=seed, n=n, sizes=tuple(range(32, 129, 16)))
+    return I.batch_workload(seed=seed, n=n)
+
+
+def build_batch(kind, n, seed, precision):
+    """Plans the batch, initialises every lattice from its own RT state (fields built on the
+    GPU), autotunes on those states, re-initialises, and returns (batch, spec, params, fa,
+    fb, tuned configuration)."""
     import torch
 
     from paper_1703_04594_gb300 import inputs as I
     from paper_1703_04594_gb300 import lbm
 
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    fp32 = a.precision == "fp32"
-    fix = a.precision == "fp64fix"
-    prec = lbm.FP32_SHIFTED if fp32 else (lbm.FP64_FIXED if fix else lbm.FP64)
-    spec = I.batch_workload(seed=4 + rank, n=a.batch_n)
+    prec = {"fp32": lbm.FP32_SHIFTED, "fp64fix": lbm.FP64_FIXED, "fp64": lbm.FP64}[precision]
+    spec = batch_lattices(kind, n, seed)
     params, fa, fb = [], [], []
     for lx, ly, tau, s in spec:
         p = lbm.Params(lx, ly, tau=tau, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP, precision=prec)
         params.append(p)
         fa.append(lbm.empty_state(p))
         fb.append(lbm.empty_state(p))
+
+    def init_all():
+        for (lx, ly, tau, s), p, t in zip(spec, params, fa):
+            lbm.init(p, *[x.contiguous() for x in I.rt_state(lx, ly, s, t_bottom=T_BOTTOM, t_top=T_TOP,
+                                                               g=abs(GY), device="cuda")], t)
+        torch.cuda.synchronize()
+
+    init_all()
     b = lbm.Batch(params, fa, fb)
-    cfg = b.autotune(trial_steps=2)                       # on the not-yet-initialised buffers
-    for (lx, ly, tau, s), p, t in zip(spec, params, fa):
-        dev = [x.contiguous().cuda() for x in I.rt_state(lx, ly, s, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY))]
-        lbm.init(p, *dev, t)
+    cfg = b.autotune(trial_steps=2)                  # advances the states: initialise again
     b.close()
+    init_all()
     b = lbm.Batch(params, fa, fb)
     b.configure(cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"])
-    sites = b.sites()
-    stream = torch.cuda.current_stream()
+    return b, spec, params, fa, fb, cfg
 
-    def timed(mode_cfg, steps):
-        b.configure(*mode_cfg)
-        b.run(a.warmup, stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.run(steps, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if b.status() != lbm.OK:
-            raise RuntimeError("batched run reported a barrier timeout")
-        return e0.elapsed_time(e1)
 
-    with ClockSampler(local) as clk:
-        ms = timed((cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"]), a.steps)
-    ms_loop = timed((lbm.BATCH_LOOP, 4, 0), a.steps)
-    value = sites * a.steps / (ms * 1e-3) / 1e6
-    bytes_site = BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64
-    kind = "fp32" if fp32 else ("fix64" if fix else "fp64")
-    if fp32 or fix:
-        achieved = bytes_site * sites * a.steps / (ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": achieved / HBM_PEAK_GBS, "traffic": None, "peak_source": HBM_PEAK_SOURCE,
-                    "kernel": ("k_batch_persistent<" if cfg["mode"] == lbm.BATCH_PERSISTENT
-                               else "k_batch_step<") + kind + ">"}
+def time_batch(b, mode_cfg, steps, warmup, graph=False):
+    """ms for `steps` steps of the batch in configuration mode_cfg = (mode, tile columns,
+    blocks per SM); with graph=True the steps are one captured CUDA graph, replayed once."""
+    import torch
+
+    from paper_1703_04594_gb300 import lbm
+
+    b.configure(*mode_cfg)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(2 * ((warmup + 1) // 2), s)            # even: the parity comes back
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.run(steps, s)
+        # the capture recorded the launches without running them; the batch's parity moved
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            e0.record(s)
+            g.replay()
+            e1.record(s)
     else:
-        achieved = FLOPS_PER_SITE_FP64 * sites * a.steps / (ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                    "kernel": ("k_batch_persistent<double>" if cfg["mode"] == lbm.BATCH_PERSISTENT
-                               else "k_batch_step<double>")}
+        with torch.cuda.stream(s):
+            e0.record(s)
+            b.run(steps, s)
+            e1.record(s)
+    torch.cuda.synchronize()
+    if b.status() != lbm.OK:
+        raise RuntimeError("batched run reported a barrier timeout")
+    return e0.elapsed_time(e1)
+
+
+def batch_roofline(precision, sites, ms_step, cfg):
+    from paper_1703_04594_gb300 import lbm
+
+    kname = {"fp32": "fp32", "fp64fix": "fix64", "fp64": "double"}[precision]
+    kernel = ("k_batch_persistent<" if cfg["mode"] == lbm.BATCH_PERSISTENT else "k_batch_step<") + kname + ">"
+    if precision == "fp64":
+        return kernel_roofline("alu", FLOPS_PER_SITE_FP64, sites, ms_step, kernel)
+    return kernel_roofline("hbm", BYTES_PER_SITE_FP32 if precision == "fp32" else BYTES_PER_SITE_FP64, sites,
+                           ms_step, kernel)
+
+
+def batch_form(a, precision, kind="uneven", n=None, seed=4):
+    """The batched workload at K steps in the autotuned configuration, against looping the
+    single-lattice kernel over the lattices (both eager launches)."""
+    import torch
+
+    from paper_1703_04594_gb300 import lbm
+
+    n = n or (1024 if kind == "small" else 256)
+    b, spec, params, fa, fb, cfg = build_batch(kind, n, seed, precision)
+    sites = b.sites()
+    tuned = (cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"])
+    with ClockSampler(0) as clk:
+        ms = time_batch(b, tuned, a.steps, a.warmup)
+    ms_loop = time_batch(b, (lbm.BATCH_LOOP, 4, 0), a.steps, a.warmup)
+    out = {"value": sites * a.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / a.steps,
+           "steps": a.steps, "dtype": {"fp32": "f32+i64+f64", "fp64fix": "f64+i64", "fp64": "f64"}[precision],
+           "workload": (f"{len(spec)} RT lattices, " +
+                        ("Lx in 32..128" if kind == "small" else "Lx in 128..1024") + ", Ly = 2 Lx, tau in [0.6, 1.0]"),
+           "sites": sites, "autotuned": cfg,
+           "loop_baseline": {"value": sites * a.steps / (ms_loop * 1e-3) / 1e6, "unit": "MLUPS",
+                             "what": "single-lattice kernel launched per lattice per step"},
+           "roofline": batch_roofline(precision, sites, ms / a.steps, cfg),
+           "gpu_launches": a.steps if cfg["mode"] == lbm.BATCH_PER_STEP else 1, "clocks": clk.summary()}
+    b.close()
+    del fa, fb
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(a):
+    """Batched workload (one JSON line): Lx drawn by seed 4 from 128..1024 (or 32..128 with
+    --batch-kind small), Ly = 2 Lx, tau ~ U[0.6, 1.0], own interface seeds.  The autotuned
+    configuration, the persistent launch and the per-step launches each run --steps steps
+    captured in one CUDA graph; the loop over the single-lattice kernel runs eagerly."""
+    import torch
+
+    from paper_1703_04594_gb300 import lbm
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    b, spec, params, fa, fb, cfg = build_batch(a.batch_kind, a.batch_n if a.batch_kind == "uneven" else 1024,
+                                               4 + rank, a.precision)
+    sites = b.sites()
+    tuned = (cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"])
+    with ClockSampler(local) as clk:
+        ms = time_batch(b, tuned, a.steps, a.warmup, graph=True)
+    modes = {}
+    for name, mc in (("persistent_graph", (lbm.BATCH_PERSISTENT, cfg["tile_columns"], 0)),
+                     ("per_step_graph", (lbm.BATCH_PER_STEP, cfg["tile_columns"], 0)),
+                     ("per_step_eager", (lbm.BATCH_PER_STEP, cfg["tile_columns"], 0)),
+                     ("loop_eager", (lbm.BATCH_LOOP, 4, 0))):
+        t = time_batch(b, mc, a.steps, a.warmup, graph=name.endswith("graph"))
+        modes[name] = {"MLUPS": sites * a.steps / (t * 1e-3) / 1e6, "ms_per_step": t / a.steps}
+    value = sites * a.steps / (ms * 1e-3) / 1e6
     if rank == 0:
         line = {"metric": "D2Q37 MLUPS (batched)", "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+i64+f64" if fp32 else ("f64+i64" if fix else "f64"),
+                "dtype": {"fp32": "f32+i64+f64", "fp64fix": "f64+i64", "fp64": "f64"}[a.precision],
                 "data": "synthetic",
-                "config": {"workload": f"{len(spec)} RT lattices, Lx in 128..1024, Ly = 2 Lx, tau in [0.6, 1.0]",
+                "config": {"workload": f"{len(spec)} RT lattices ({a.batch_kind}), Ly = 2 Lx, tau in [0.6, 1.0]",
                            "sites": sites, "precision": a.precision, "autotuned": cfg,
-                           "l2": "states total >> 129 MB L2"},
-                "loop_baseline": {"value": sites * a.steps / (ms_loop * 1e-3) / 1e6, "unit": "MLUPS",
-                                  "what": "single-lattice kernel launched per lattice per step"},
-                "roofline": roofline, "gpu_launches": a.steps if cfg["mode"] == lbm.BATCH_PER_STEP else 1,
+                           "timed": f"{a.steps} steps in one CUDA graph",
+                           "l2": "states total >> 129 MB L2" if sites > 1e7 else "states partly L2-resident"},
+                "modes": modes,
+                "roofline": batch_roofline(a.precision, sites, ms / a.steps, cfg),
+                "gpu_launches": a.steps if cfg["mode"] == lbm.BATCH_PER_STEP else 1,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     b.close()
 
 
-def run_adjoint(a):
-    """Differentiation workload: dE/d(a_1..a_8, tau) of the total kinetic energy after 500
-    FP64 steps of a 512 x 1024 RT lattice (seed 5), checkpoints every 22 steps, against the
-    plain forward run of the same 500 steps."""
+ADJ_LX, ADJ_LY, ADJ_N, ADJ_EVERY = 512, 1024, 500, 22
+# algorithmic bytes per site of one adjoint step: the gathered f~ (37 x 8), lambda^{n+1}
+# read (37 x 8) and lambda^n written (37 x 8)
+BYTES_PER_SITE_ADJ = 888
+
+
+def adjoint_form(a, repeats, precision="fp64", seed=5):
+    """dE/d(a_1..a_8, tau) of the total kinetic energy after 500 steps of a 512 x 1024 RT
+    lattice, checkpoints every 22 steps, against the plain forward run; and the adjoint step
+    kernel alone against its HBM roofline."""
     import torch
 
     from paper_1703_04594_gb300 import adjoint as A
     from paper_1703_04594_gb300 import inputs as I
     from paper_1703_04594_gb300 import lbm
 
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    lx, ly, n, every, seed = 512, 1024, 500, 22, 5 + rank
-    fix = a.precision == "fp64fix"   # forward steps with the fixed-point relaxation
+    lx, ly, n, every = ADJ_LX, ADJ_LY, ADJ_N, ADJ_EVERY
     p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
-                   precision=lbm.FP64_FIXED if fix else lbm.FP64)
+                   precision=lbm.FP64_FIXED if precision == "fp64fix" else lbm.FP64)
     modes = I.rt_modes(lx, ly, seed)
 
     def forward_only():
@@ -498,33 +667,78 @@ def run_adjoint(a):
         e.backward()
         return amp.grad, tau.grad
 
-    for _ in range(max(1, a.warmup)):
-        forward_only()
-        gradient()
-    with ClockSampler(local) as clk:
+    forward_only()
+    gradient()
+    with ClockSampler(0) as clk:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(a.steps):
+        for _ in range(repeats):
             forward_only()
         torch.cuda.synchronize()
-        t_fwd = max_over_ranks((time.perf_counter() - t0) / a.steps, "cuda")
+        t_fwd = (time.perf_counter() - t0) / repeats
         t0 = time.perf_counter()
-        for _ in range(a.steps):
+        for _ in range(repeats):
             gradient()
         torch.cuda.synchronize()
-        t_grad = max_over_ranks((time.perf_counter() - t0) / a.steps, "cuda")
+        t_grad = (time.perf_counter() - t0) / repeats
+    # the adjoint step alone (collide VJP with the transposed propagate, wall slots, tau
+    # partials): CUDA events over back-to-back calls on a mid-run state
+    p64 = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
+    fields = [t.contiguous().cuda() for t in I.rt_fields(lx, ly, modes, T_BOTTOM, T_TOP, abs(GY))]
+    f = lbm.empty_state(p64)
+    lbm.init(p64, *fields, f)
+    f = lbm.run(p64, f, lbm.empty_state(p64), 100).clone()
+    lam = [lbm.empty_state(p64), lbm.empty_state(p64)]
+    lbm.kinetic_energy_grad(p64, f, lam[0])
+    work = lbm.adjoint_work(p64)
+    dtau = torch.zeros((), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(4):
+        lbm.adjoint_step(p64, f, lam[k % 2], lam[(k + 1) % 2], dtau, work, stream)
+    calls = 40
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(0) as aclk:
+        ev[0].record(stream)
+        for k in range(calls):
+            lbm.adjoint_step(p64, f, lam[k % 2], lam[(k + 1) % 2], dtau, work, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    ms_adj = ev[0].elapsed_time(ev[1]) / calls
+    sites = lx * ly
+    return {"value": whole_job_mlups(sites, n, 1, t_grad * 1e3), "unit": "MLUPS",
+            "what": "MLUPS of the whole gradient: forward run with checkpoints, then recomputation and the "
+                    "adjoint step per segment, per site and forward step",
+            "workload": f"dE/d(a_1..a_8, tau), E = kinetic energy after {n} steps of {lx}x{ly}, checkpoints "
+                        f"every {every}", "repeats": repeats,
+            "forward_steps": "fixed-point relaxation" if precision == "fp64fix" else "float64",
+            "gradient_s": t_grad, "forward_s": t_fwd, "gradient_over_forward": t_grad / t_fwd,
+            "forward_baseline": {"value": whole_job_mlups(sites, n, 1, t_fwd * 1e3), "unit": "MLUPS",
+                                 "what": "the same 500 forward steps and the energy, no gradient"},
+            "adjoint_step_ms": ms_adj,
+            "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms_adj,
+                                        "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
+                                        TRAFFIC_BYTES_PER_LAUNCH.get("adjoint")),
+            "clocks": clk.summary(), "adjoint_step_clocks": aclk.summary()}
+
+
+def run_adjoint(a):
+    """Differentiation workload (one JSON line): the gradient of the kinetic energy after 500
+    steps of a 512 x 1024 RT lattice (seed 5), checkpoints every 22 steps."""
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    r = adjoint_form(a, repeats=max(1, a.steps), precision=a.precision, seed=5 + rank)
     if rank == 0:
-        sites = lx * ly
-        line = {"metric": "D2Q37 MLUPS (gradient: forward + checkpointed adjoint)",
-                "value": whole_job_mlups(sites, n, world, t_grad * 1e3), "unit": "MLUPS", "n_gpus": world,
-                "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_grad * 1e3 / n, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if fix else "f64",
+        line = {"metric": "D2Q37 MLUPS (gradient: forward + checkpointed adjoint)", "value": r["value"],
+                "unit": "MLUPS", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": r["gradient_s"] * 1e3 / ADJ_N, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64+i64" if a.precision == "fp64fix" else "f64",
                 "data": "synthetic",
-                "config": {"workload": f"dE/d(a_1..a_8, tau), E = kinetic energy after {n} steps of {lx}x{ly}",
-                           "checkpoint_every": every, "repeats": a.steps,
-                           "forward_steps": "fixed-point relaxation" if fix else "float64"},
-                "forward_s": t_fwd, "gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
-                "clocks": clk.summary()}
+                "config": {"workload": r["workload"], "checkpoint_every": ADJ_EVERY, "repeats": r["repeats"],
+                           "forward_steps": r["forward_steps"]},
+                **{k: r[k] for k in ("forward_s", "gradient_s", "gradient_over_forward", "forward_baseline",
+                                     "adjoint_step_ms", "roofline", "clocks")}}
         print(json.dumps(line), flush=True)
 
 

@@ -48,7 +48,12 @@ extern "C" {
 
 enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, LBM_ENOMEM = 4, LBM_ESIZE = 5 };
 /* LBM_FP64: float64 populations, float64 collision arithmetic (moment sums in exact 64-bit
- * fixed point).  LBM_FP32_SHIFTED: float32 storage of f_i - w_i rho0.  LBM_FP64_FIXED:
+ * fixed point for sites whose populations are all below 8 in magnitude, plain float64 sums
+ * for any other site, so every finite state is handled; a non-finite population makes its
+ * site's outputs NaN).  LBM_FP32_SHIFTED: float32 storage of g_i = f_i - w_i rho0, for
+ * states with every |g_i| < 8 (choose rho0 near the state's density); a site holding a
+ * larger deviation, an infinity or a NaN gets NaN moments, and every population it
+ * produces is NaN.  LBM_FP64_FIXED:
  * float64 populations as LBM_FP64 (same buffers, interchangeable states); the fused step
  * evaluates the equilibrium polynomial and the relaxation of every population in 64-bit
  * fixed point on the integer pipes, with errors below one float64 rounding unit, for sites
@@ -142,7 +147,9 @@ int32_t lbm_kinetic_energy(const lbm_params* p, const void* f_dev, double* out_d
  * the library holds until the process exits.  A lattice needs ceil(ly/32) * ceil(lx/4)
  * tiles (4096 x 8192 needs exactly the maximum); larger lattices return LBM_ESIZE.
  * The first call on each device looks up the array's device address (and may load the
- * library's device code); make that first call before any stream capture.  All calls share
+ * library's device code); make that first call before any stream capture.  The address is
+ * kept for the life of the process: after cudaDeviceReset on a device, do not call this
+ * entry point on that device again (the array may have moved).  All calls share
  * the array and leave their partial sums in it; each call only reads what it has just
  * written, so no clearing is needed, but calls whose kernels can overlap on the GPU (on
  * different streams without ordering) race on it. */
@@ -218,7 +225,8 @@ enum lbm_batch_mode {
   LBM_BATCH_LOOP = 3        /* the single-lattice kernel launched per lattice (baseline) */
 };
 /* Validates n lattices and binds their buffers (f_a_dev[j], f_b_dev[j]: device states of
- * lbm_buffer_bytes(&params[j]) bytes, current state in f_a).  Allocates the batch's own
+ * lbm_buffer_bytes(&params[j]) bytes, current state in f_a; no two of the 2n buffers may
+ * overlap, else LBM_EINVAL).  Allocates the batch's own
  * device descriptor table, tile table and barrier word (freed by lbm_batch_destroy).  Synchronous.  Default configuration: persistent, tiles of 32 x 4,
  * as many blocks per SM as fit.  At most 65535 lattices. */
 int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a_dev, void* const* f_b_dev, int32_t n,
@@ -240,8 +248,9 @@ int32_t lbm_batch_run(lbm_batch* b, int32_t n_steps, void* stream);
 int32_t lbm_batch_parity(const lbm_batch* b);
 /* Total fluid sites of the batch. */
 int64_t lbm_batch_sites(const lbm_batch* b);
-/* Synchronous: LBM_OK, or LBM_ETIMEOUT if a persistent run's grid-barrier wait expired
- * (the run then stopped early and the states are undefined); clears the error word. */
+/* Synchronous: LBM_OK, or LBM_ETIMEOUT if the grid-barrier wait of any persistent run since
+ * the previous call expired (that run stopped early and the states are undefined); clears
+ * the flag.  A later run does not erase an earlier run's timeout. */
 int32_t lbm_batch_status(lbm_batch* b);
 /* Grid-barrier wait limit in ns (default 2 s, at most 60 s).  phantom_arrivals makes every
  * barrier wait for that many extra blocks that never arrive: a test hook that forces the

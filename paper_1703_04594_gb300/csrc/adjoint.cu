@@ -162,6 +162,13 @@ __device__ __noinline__ void gather_to_shared(const double* __restrict__ fin, co
   for (int i = 0; i < Q; ++i) sf[i * 32] = f[i];
 }
 
+// Float64 moments of a staged site (populations sf[i * 32]), for sites outside the
+// fixed-point sums' range; not inlined, so the common path keeps its registers.
+__device__ __noinline__ void moments_float64_staged(const double* sf, double& rho, double& jx, double& jy,
+                                                     double& e) {
+  moments_float64([&](int i) { return sf[i * 32]; }, rho, jx, jy, e);
+}
+
 __device__ __forceinline__ void cp_async8_adj(double* smem_dst, const double* gmem_src) {
   const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gmem_src) : "memory");
@@ -202,7 +209,8 @@ __global__ void __launch_bounds__(128, 5) k_adj_collide(const double* __restrict
     const auto fget = [&](int i) { return sf[i * 32]; };
     if (active) {
       double rho, jx, jy, e;
-      moments_get(fget, rho, jx, jy, e, [](int, int) {});
+      moments_get_or(fget, rho, jx, jy, e, [](int, int) {},
+                     [&](double& r, double& mx, double& my, double& me) { moments_float64_staged(sf, r, mx, my, me); });
       const double inv = 1.0 / rho;
       const double Jx = C * jx, Jy = C * jy, E = C2 * e;  // xi-unit moments
       const double ux = Jx * inv, uy = Jy * inv;

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "../../include/lbm_d2q37.h"
@@ -44,17 +45,21 @@ struct BatchLattice {
   int tiles_x;           // ceil(lx / TX)
 };
 
+// The first three words are reset by every persistent launch; `sticky` is not.
 struct BatchSync {
   unsigned int arrived;  // grid-barrier arrivals since the launch started
-  unsigned int error;    // 1 after a barrier wait expired
+  unsigned int error;    // 1 after a barrier wait of this launch expired (stops every block)
   unsigned int step;     // step whose barrier expired
-  unsigned int pad;
+  unsigned int sticky;   // 1 after any launch's wait expired, until lbm_batch_status reads it
 };
+constexpr size_t kBatchSyncLaunchBytes = 3 * sizeof(unsigned int);
 
 namespace {
 
 // Step kinds: the strip functions of the three storage/arithmetic forms.
-enum BatchKind { kFp64 = 0, kFp32 = 1, kFix64 = 2 };
+// kFp32Scaled: FP32 storage where some lattice has a reference density of 2 or more (the
+// moment sums read each lattice's scale constants; see step_fp32.cuh).
+enum BatchKind { kFp64 = 0, kFp32 = 1, kFix64 = 2, kFp32Scaled = 3 };
 
 template <int K>
 struct KindOf {
@@ -62,6 +67,10 @@ struct KindOf {
 };
 template <>
 struct KindOf<kFp32> {
+  using T = float;
+};
+template <>
+struct KindOf<kFp32Scaled> {
   using T = float;
 };
 
@@ -89,7 +98,7 @@ __device__ __forceinline__ void batch_tile(const BatchLattice* __restrict__ L, c
   if constexpr (KIND == kFp64) step_strip_fp64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
   else if constexpr (KIND == kFix64)
     step_strip_fix64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld, staged + threadIdx.y * (Q * 32));
-  else step_strip_fp32<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
+  else step_strip_fp32<PERIODIC, KIND == kFp32Scaled>(src, dst, B.a, B.a, x, ty * 32, ld);
 }
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -123,6 +132,7 @@ __device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, l
       }
       if ((long long)(global_ns() - t0) > timeout_ns || ++it > max_iter) {
         if (atomicCAS(&sync->error, 0u, 1u) == 0u) atomicExch(&sync->step, (unsigned)step);
+        atomicExch(&sync->sticky, 1u);
         ok = 0;
         break;
       }
@@ -174,6 +184,7 @@ struct lbm_batch {
   int n = 0;
   int precision = LBM_FP64;
   int periodic = 0;
+  int fp32_scaled = 0;  // FP32 batch with some reference density of 2 or more
   long long total_tiles = 0;
   unsigned short* dev_tile_lattice = nullptr;  // lattice of every tile
   size_t tile_table_cap = 0;
@@ -201,7 +212,8 @@ int32_t cuda_status(cudaError_t e) {
 }
 
 int kind_of(const lbm_batch* b) {
-  return b->precision == LBM_FP64_FIXED ? kFix64 : (b->precision == LBM_FP32_SHIFTED ? kFp32 : kFp64);
+  if (b->precision == LBM_FP32_SHIFTED) return b->fp32_scaled ? kFp32Scaled : kFp32;
+  return b->precision == LBM_FP64_FIXED ? kFix64 : kFp64;
 }
 
 template <int K>
@@ -217,6 +229,7 @@ void* persistent_kernel(const lbm_batch* b) {
   switch (kind_of(b)) {
     case kFix64: return persistent_fn<kFix64>(b->periodic);
     case kFp32: return persistent_fn<kFp32>(b->periodic);
+    case kFp32Scaled: return persistent_fn<kFp32Scaled>(b->periodic);
     default: return persistent_fn<kFp64>(b->periodic);
   }
 }
@@ -224,6 +237,7 @@ void* per_step_kernel(const lbm_batch* b) {
   switch (kind_of(b)) {
     case kFix64: return per_step_fn<kFix64>(b->periodic);
     case kFp32: return per_step_fn<kFp32>(b->periodic);
+    case kFp32Scaled: return per_step_fn<kFp32Scaled>(b->periodic);
     default: return per_step_fn<kFp64>(b->periodic);
   }
 }
@@ -273,7 +287,7 @@ int32_t launch_persistent(lbm_batch* b, int steps, cudaStream_t s) {
   const int per_sm = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, fit) : fit;
   const unsigned grid = (unsigned)(per_sm * b->sms);
   if ((unsigned long long)steps * grid + b->phantom >= 0x7fffffffULL) return LBM_EINVAL;
-  int32_t st = cuda_status(cudaMemsetAsync(b->dev_sync, 0, sizeof(BatchSync), s));
+  int32_t st = cuda_status(cudaMemsetAsync(b->dev_sync, 0, kBatchSyncLaunchBytes, s));
   if (st != LBM_OK) return st;
   const BatchLattice* L = b->dev_lattices;
   const unsigned short* tl = b->dev_tile_lattice;
@@ -379,9 +393,26 @@ int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a, void* const* 
     BatchLattice L;
     memset(&L, 0, sizeof(L));
     L.a = make_step_args(p);
+    if (L.a.fix_back != 1.0 / 4503599627370496.0) b->fp32_scaled = 1;
     L.f[0] = f_a[j];
     L.f[1] = f_b[j];
     b->host.push_back(L);
+  }
+  // no two of the 2n state buffers may overlap (a step reads one lattice's buffer while
+  // other blocks write another's)
+  {
+    std::vector<std::pair<uintptr_t, uintptr_t>> ranges;
+    for (int j = 0; j < n; ++j) {
+      const uintptr_t bytes = (uintptr_t)lbm_buffer_bytes(&params[j]);
+      ranges.push_back({(uintptr_t)f_a[j], (uintptr_t)f_a[j] + bytes});
+      ranges.push_back({(uintptr_t)f_b[j], (uintptr_t)f_b[j] + bytes});
+    }
+    std::sort(ranges.begin(), ranges.end());
+    for (size_t k = 1; k < ranges.size(); ++k)
+      if (ranges[k].first < ranges[k - 1].second) {
+        delete b;
+        return LBM_EINVAL;
+      }
   }
   cudaDeviceProp prop;
   if (cudaGetDevice(&b->device) != cudaSuccess || cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) {
@@ -492,7 +523,7 @@ int32_t lbm_batch_status(lbm_batch* b) {
   BatchSync h;
   const int32_t st = cuda_status(cudaMemcpy(&h, b->dev_sync, sizeof(h), cudaMemcpyDeviceToHost));
   if (st != LBM_OK) return st;
-  if (h.error) {
+  if (h.sticky) {
     cudaMemset(b->dev_sync, 0, sizeof(BatchSync));
     return LBM_ETIMEOUT;
   }

@@ -37,8 +37,12 @@ struct CollideConst {
 // the fixed-point sums are exact, and the four sums are converted back to float64.  The
 // error is at most 37 * 2^-53 absolute per moment, the same order as a float64
 // summation, and it is order-independent.  This takes 88 additions off the FP64 pipe.
-// Valid while sum_i |v_i|^2 |f_i| < 2048 (physical states: rho below ~200).
+// The signed 64-bit sums hold magnitudes below 2^11.  With every |f_i| < 8 the largest
+// of them, sum |v_i|^2 |f_i|, stays below 216 * 8 = 1728 (216 = sum_i |v_i|^2), so the
+// fixed-point sums are used only then; a site with a population of magnitude 8 or more
+// (a dense state, rho above ~30, or an infinity or NaN) sums in plain float64 instead.
 constexpr int DFIX = 52;
+constexpr int kFixSumMaxExp = 1025;  // largest biased exponent with |f| < 8
 
 // Also returns the biased exponent field E of v.
 __device__ __forceinline__ long long to_fix52_e(double v, int& E) {
@@ -55,14 +59,36 @@ __device__ __forceinline__ long long to_fix52_e(double v, int& E) {
   return (x ^ s) - s;
 }
 
+// The same four moments as plain float64 sums over opposite pairs (P = f_v + f_-v and
+// M = f_v - f_-v, times the integer velocity weights).  Reads every f_i again through fget.
+template <class Fget>
+__device__ __forceinline__ void moments_float64(Fget&& fget, double& rho, double& jx, double& jy, double& e) {
+  double R = fget(0), Ei = 0.0, Jx = 0.0, Jy = 0.0;
+#pragma unroll
+  for (int k = 1; k <= NPAIR; ++k) {
+    const double a = fget(k), b = fget(k + NPAIR);
+    const double P = a + b, M = a - b;
+    R += P;
+    Ei = fma((double)v2(k), P, Ei);
+    if (rep_vx(k) != 0) Jx = fma((double)rep_vx(k), M, Jx);
+    if (rep_vy(k) != 0) Jy = fma((double)rep_vy(k), M, Jy);
+  }
+  rho = R;
+  e = Ei;
+  jx = Jx;
+  jy = Jy;
+}
+
 // Streaming accumulation: each opposite pair is converted and added to the four sums
 // at once, so only the sums stay live (the products by the small integer velocity
 // weights are exact integer shifts and adds).  on_exp(i, E) sees the exponent field of
 // every f_i (for range checks of callers; a no-op otherwise).
 // `fget(i)` returns f_i (an array read, or a load); it is called once per population.
-template <class Fget, class OnExp>
-__device__ __forceinline__ void moments_get(Fget&& fget, double& rho, double& jx, double& jy, double& e,
-                                            OnExp&& on_exp) {
+// `wide(rho, jx, jy, e)` computes the moments of a site outside the fixed-point sums'
+// range (moments_float64 on the same values, possibly out of line).
+template <class Fget, class OnExp, class Wide>
+__device__ __forceinline__ void moments_get_or(Fget&& fget, double& rho, double& jx, double& jy, double& e,
+                                               OnExp&& on_exp, Wide&& wide) {
   int E0, Ea, Eb;
   long long R = to_fix52_e(fget(0), E0), Ei = 0, Jx = 0, Jy = 0;
   on_exp(0, E0);
@@ -84,10 +110,16 @@ __device__ __forceinline__ void moments_get(Fget&& fget, double& rho, double& jx
   e = (double)Ei * S;
   jx = (double)Jx * S;
   jy = (double)Jy * S;
-  // a population of magnitude 2^11 or more (an infinity, a NaN, or far outside any
-  // physical state) has no fixed-point form: the moments become NaN, so the site's
-  // outputs are NaN too, as a float64 sum would make them
-  if (emax > 1033) rho = e = jx = jy = __longlong_as_double(0x7FF8000000000000LL);
+  // outside the fixed-point sums' range (see kFixSumMaxExp): plain float64 sums, which
+  // also carry infinities and NaNs into the moments as any float64 sum would
+  if (emax > kFixSumMaxExp) wide(rho, jx, jy, e);
+}
+
+template <class Fget, class OnExp>
+__device__ __forceinline__ void moments_get(Fget&& fget, double& rho, double& jx, double& jy, double& e,
+                                            OnExp&& on_exp) {
+  moments_get_or(fget, rho, jx, jy, e, on_exp,
+                 [&](double& r, double& x, double& y, double& en) { moments_float64(fget, r, x, y, en); });
 }
 
 __device__ __forceinline__ void moments_int(const double (&f)[Q], double& rho, double& jx, double& jy, double& e) {

@@ -17,6 +17,12 @@ struct StepScalars {
   CollideConst cc;
   double rho0;          // FP32 shifted storage: g_i = f_i - w_i rho0
   float f_omega, f_om1, f_cgx, f_cgy;  // float copies of cc for the FP32 collision
+  // FP32 moment sums: of g_i 2^(52-k), 2^k <= rho0 < 2^(k+1) (k >= 0), valid for
+  // |g_i| < f_fix_range = 8 * 2^k; split constants 48 * 2^k, 1.5 * 2^(k-18), 2^(52-k)
+  // (step_fp32.cuh); fix_back = 2^(k-52) turns the sums into moments
+  float f_split_c1, f_split_c2, f_split_s, f_fix_range, f_fix_back;
+  int i_split_b1, i_split_b2;  // bit patterns of f_split_c1, f_split_c2
+  double fix_back;
 };
 
 // Wall tables, read only by the warps next to a wall.

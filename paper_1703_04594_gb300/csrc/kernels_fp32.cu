@@ -8,15 +8,15 @@
 
 namespace d2q37 {
 
-template <bool PERIODIC>
 #ifndef LBM_FP32_MIN_BLOCKS
 #define LBM_FP32_MIN_BLOCKS 6  // 80 registers; measured best among 4..8 blocks per SM
 #endif
+template <bool PERIODIC, bool SCALED>
 __global__ void __launch_bounds__(128, LBM_FP32_MIN_BLOCKS) k_step_fp32(const float* __restrict__ fin,
                                                                        float* __restrict__ fout, StepArgs a) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   if (x >= a.lx) return;  // uniform per warp
-  step_strip_fp32<PERIODIC>(fin, fout, a, a, x, blockIdx.x * 32, LdReadOnly());
+  step_strip_fp32<PERIODIC, SCALED>(fin, fout, a, a, x, blockIdx.x * 32, LdReadOnly());
 }
 
 // g_i = f_i^eq(rho, u, T) - w_i rho0, equilibrium evaluated in float64 then rounded.
@@ -36,14 +36,15 @@ __global__ void __launch_bounds__(128) k_init_fp32(const double* __restrict__ rh
              [&](int i, double v) { dst[i * a.pop] = (float)(v - weight(i) * rho0); });
 }
 
-__device__ __forceinline__ void site_fields_fp32(const float (&g)[Q], double rho0, double& rho, double& ux,
+__device__ __forceinline__ void site_fields_fp32(const float (&g)[Q], const StepScalars& a, double& rho, double& ux,
                                                  double& uy, double& T) {
-  const FixMoments m = moments_fix(g);
-  rho = fma((double)m.drho, FIX_SCALE, rho0);
+  const double rho0 = a.rho0;
+  const DevMoments<double> m = moments_fix<double, true>(g, a);
+  rho = m.drho + rho0;
   const double inv = 1.0 / rho;
-  ux = C * ((double)m.jx * FIX_SCALE) * inv;
-  uy = C * ((double)m.jy * FIX_SCALE) * inv;
-  const double etot = fma((double)m.de, FIX_SCALE, rho0 * (D / C2));
+  ux = C * m.jx * inv;
+  uy = C * m.jy * inv;
+  const double etot = m.de + rho0 * (D / C2);
   T = (C2 * etot * inv - fma(ux, ux, uy * uy)) / D;
 }
 
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(128) k_moments_fp32(const float* __restrict__ 
 #pragma unroll
   for (int i = 0; i < Q; ++i) g[i] = __ldg(fin + o + i * a.pop);
   const long long fi = (long long)x * a.ly + y;
-  site_fields_fp32(g, a.rho0, rho[fi], ux[fi], uy[fi], T[fi]);
+  site_fields_fp32(g, a, rho[fi], ux[fi], uy[fi], T[fi]);
 }
 
 __global__ void __launch_bounds__(128) k_ke_partial_fp32(const float* __restrict__ fin, double* __restrict__ part,
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(128) k_ke_partial_fp32(const float* __restrict
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = __ldg(fin + o + i * a.pop);
     double rho, ux, uy, T;
-    site_fields_fp32(g, a.rho0, rho, ux, uy, T);
+    site_fields_fp32(g, a, rho, ux, uy, T);
     ke = 0.5 * rho * fma(ux, ux, uy * uy);
   }
 #pragma unroll
@@ -88,8 +89,14 @@ static inline dim3 site_grid(const StepArgs& a) { return dim3((a.ly + 31) / 32, 
 static const dim3 kSiteBlock(32, 4);
 
 cudaError_t launch_step_fp32(const float* fin, float* fout, const StepArgs& a, cudaStream_t s) {
-  if (a.periodic) k_step_fp32<true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
-  else k_step_fp32<false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+  const bool scaled = a.fix_back != 1.0 / 4503599627370496.0;
+  if (a.periodic) {
+    if (scaled) k_step_fp32<true, true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+    else k_step_fp32<true, false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+  } else {
+    if (scaled) k_step_fp32<false, true><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+    else k_step_fp32<false, false><<<site_grid(a), kSiteBlock, 0, s>>>(fin, fout, a);
+  }
   return cudaGetLastError();
 }
 

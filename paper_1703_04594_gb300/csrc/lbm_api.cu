@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cmath>
+
 #include "../../include/lbm_d2q37.h"
 #include "kernels.h"
 
@@ -85,6 +87,16 @@ StepArgs d2q37::make_step_args(const lbm_params* p) {
   a.f_om1 = (float)a.cc.om1;
   a.f_cgx = (float)a.cc.cgx;
   a.f_cgy = (float)a.cc.cgy;
+  int k = 0;  // 2^k <= rho0 < 2^(k+1), k >= 0
+  while (k < 100 && p->rho0 >= std::ldexp(1.0, k + 1)) ++k;
+  a.f_split_c1 = (float)std::ldexp(48.0, k);
+  a.f_split_c2 = (float)std::ldexp(1.5, k - 18);
+  a.f_split_s = (float)std::ldexp(1.0, 52 - k);
+  a.f_fix_range = (float)std::ldexp(8.0, k);
+  memcpy(&a.i_split_b1, &a.f_split_c1, sizeof(int));
+  memcpy(&a.i_split_b2, &a.f_split_c2, sizeof(int));
+  a.fix_back = std::ldexp(1.0, k - 52);
+  a.f_fix_back = (float)a.fix_back;
   for (int i = 0; i < Q; ++i) {
     a.wall_b[i] = wall_multiplier(i, p->t_bottom);
     a.wall_t[i] = wall_multiplier(i, p->t_top);

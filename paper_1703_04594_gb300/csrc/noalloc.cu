@@ -29,7 +29,8 @@ double* g_partials_dev[kMaxDevices] = {};  // device address of g_ke_partials, p
 
 // Device address of the array on the current device.  In host code the name
 // g_ke_partials is only a host-side stand-in, so the address has to be looked up once
-// per device with that device current.
+// per device with that device current.  The cached address is not refreshed after a
+// cudaDeviceReset (the header says so).
 int32_t partials_on_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

@@ -5,7 +5,12 @@
 //    stored float of magnitude >= 2^-29 splits exactly into three int32 parts (split3),
 //    the integer sums are exact and order-independent (error <= 37 * 2^-53 from the tiny
 //    values, the same order as a float64 accumulation), and the sums are then converted
-//    to float64;
+//    to float64.  The values summed are g_i 2^-k with 2^k <= rho0 < 2^(k+1) (k >= 0), so
+//    range and resolution follow the reference density.  The fixed-point sums hold
+//    magnitudes below 2^11, and sum |v_i|^2 |g_i 2^-k| < 216 * 8 when every
+//    |g_i| < 8 * 2^k: that is the storage range of the form, |f_i - w_i rho0| < 8 * 2^k,
+//    between 4 rho0 and 8 rho0 for rho0 >= 1.  A site outside it, or holding an infinity
+//    or NaN, gets NaN moments and so NaN in every population;
 //  * density, energy and the temperature t = T_s - 1 (the equilibrium's temperature
 //    terms) are formed in float64 from those sums; 1/rho is a float32 seed refined by one
 //    float64 Newton step;
@@ -13,46 +18,52 @@
 //    deviation form  g_i' = (1 - 1/tau) g_i + (1/tau) (f_i^eq - w_i rho0),
 //    f_i^eq - w_i rho0 = w_i [ (rho - rho0) + rho (P_i(s) - 1) ],
 //    so float32 rounds deviations, not whole populations.
-// Valid range of the storage: |f_i - w_i rho0| < 16.
 #pragma once
 #include "step_fp64.cuh"
 
 namespace d2q37 {
 
 
-constexpr int FIX = 52;                                   // fixed-point fraction bits
-constexpr double FIX_SCALE = 1.0 / 4503599627370496.0;    // 2^-52
-constexpr float FIX_SCALE_F = 1.0f / 4503599627370496.0f;
 
-// Exact split of a float |v| < 16 into three integers with v * 2^52 = H * 2^34 + R * 2^11 + L
-// (|H|, |R| <= 2^22, |L| <= 2^10), done with float additions of power-of-two constants so
-// that it runs on the FMA pipe instead of the integer pipe:
-//   h1 = fl(v + 48) lies in [32, 64), where floats are spaced 2^-18 apart, so it rounds v to
-//   a multiple of 2^-18, and within that binade the bit pattern grows by one per 2^-18:
-//   H = bits(h1) - bits(48).  r1 = v - (h1 - 48) is exact (|r1| <= 2^-19).  The same with
-//   1.5 * 2^-18 (binade [2^-18, 2^-17), spacing 2^-41) gives R and an exact rest r2,
-//   |r2| <= 2^-42, and one FMA with 1.5 * 2^23 rounds r2 * 2^52 to the integer L.
-// Floats of magnitude >= 2^-29 convert exactly; smaller ones are rounded at 2^-52.
+// Exact split of a float |v| < 16 * 2^k into three integers with
+// v * 2^(52-k) = H * 2^34 + R * 2^11 + L (|H|, |R| <= 2^22, |L| <= 2^10), done with float
+// additions of power-of-two constants so that it runs on the FMA pipe instead of the
+// integer pipe (k is the lattice's scale exponent, StepScalars::f_fix_range; k = 0 for
+// rho0 <= 1, and the constants are then 48, 1.5 * 2^-18 and 2^52):
+//   h1 = fl(v + 48 * 2^k) lies in [32, 64) 2^k, where floats are spaced 2^(k-18) apart, so
+//   it rounds v to a multiple of 2^(k-18), and within that binade the bit pattern grows by
+//   one per 2^(k-18): H = bits(h1) - bits(48 * 2^k).  r1 = v - (h1 - 48 * 2^k) is exact
+//   (|r1| <= 2^(k-19)).  The same with 1.5 * 2^(k-18) (binade [2^(k-18), 2^(k-17)), spacing
+//   2^(k-41)) gives R and an exact rest r2, |r2| <= 2^(k-42), and one FMA with 1.5 * 2^23
+//   rounds r2 * 2^(52-k) to the integer L.
+// Floats of magnitude >= 2^(k-29) convert exactly; smaller ones are rounded at 2^(k-52).
 struct Fix3 {
   int H, R, L;
 };
 
-__device__ __forceinline__ Fix3 split3(float v) {
-  constexpr float C1 = 48.0f;                   // 1.5 * 2^5
-  constexpr float C2 = 5.7220458984375e-06f;    // 1.5 * 2^-18
-  constexpr float C3 = 12582912.0f;             // 1.5 * 2^23
-  constexpr float S52 = 4503599627370496.0f;    // 2^52
-  const float h1 = __fadd_rn(v, C1);
-  const float r1 = __fsub_rn(v, __fsub_rn(h1, C1));
-  const float h2 = __fadd_rn(r1, C2);
-  const float r2 = __fsub_rn(r1, __fsub_rn(h2, C2));
-  const float h3 = __fmaf_rn(r2, S52, C3);
-  return {__float_as_int(h1) - __float_as_int(C1), __float_as_int(h2) - __float_as_int(C2),
-          __float_as_int(h3) - __float_as_int(C3)};
+// The split constants of one lattice: 48 * 2^k, 1.5 * 2^(k-18) and 2^(52-k), and the bit
+// patterns of the first two.
+struct SplitConst {
+  float c1, c2, s;
+  int b1, b2;
+};
+
+__device__ __forceinline__ Fix3 split3(float v, const SplitConst& k) {
+  constexpr float C3 = 12582912.0f;  // 1.5 * 2^23
+  const float h1 = __fadd_rn(v, k.c1);
+  const float r1 = __fsub_rn(v, __fsub_rn(h1, k.c1));
+  const float h2 = __fadd_rn(r1, k.c2);
+  const float r2 = __fsub_rn(r1, __fsub_rn(h2, k.c2));
+  const float h3 = __fmaf_rn(r2, k.s, C3);
+  return {__float_as_int(h1) - k.b1, __float_as_int(h2) - k.b2, __float_as_int(h3) - __float_as_int(C3)};
 }
 
-struct FixMoments {
-  long long drho, jx, jy, de;  // sum g, sum vx g, sum vy g, sum |v|^2 g  (all * 2^52)
+// Moments of the stored deviations: sum g, sum vx g, sum vy g, sum |v|^2 g.  The step
+// uses the momentum in float32 (JT = float), the moments kernels in float64.
+template <class JT>
+struct DevMoments {
+  double drho, de;
+  JT jx, jy;
 };
 
 __device__ __forceinline__ long long join3(int H, int R, int L) {
@@ -60,14 +71,30 @@ __device__ __forceinline__ long long join3(int H, int R, int L) {
 }
 
 // Streaming: each opposite pair is split and added to the four sums at once, in three
-// int32 lanes per sum (no overflow for |g| < 16: |sum| < 108 * 2^23 per lane).
-__device__ __forceinline__ FixMoments moments_fix(const float (&g)[Q]) {
-  const Fix3 z = split3(g[0]);
+// int32 lanes per sum.  The sums are of g_i 2^(52-k) with 2^k <= rho0 < 2^(k+1) (k = 0
+// for rho0 < 2), so their range and resolution follow the reference density: with every
+// |g_i| < 8 * 2^k no lane overflows (|sum| < 216 * 2^22 per lane)
+// and the joined 64-bit sums stay below 2^63 (see the file header).  That is the storage
+// range of the form, |g_i| < 8 * 2^k: a site holding a larger deviation, an infinity or a
+// NaN gets NaN moments, so every population it produces is NaN.  (A float64 fallback for
+// such sites does not fit the step's 80-register budget.)
+// SCALED = false is the common case k = 0 (rho0 < 2), with every constant an immediate;
+// SCALED = true reads the lattice's constants (a separate instantiation, so the common
+// one keeps its registers).
+template <class JT, bool SCALED>
+__device__ __forceinline__ DevMoments<JT> moments_fix(const float (&g)[Q], const StepScalars& a) {
+  constexpr SplitConst s0 = {48.0f, 5.7220458984375e-06f, 4503599627370496.0f, 0x42400000, 0x36c00000};
+  const SplitConst s = SCALED ? SplitConst{a.f_split_c1, a.f_split_c2, a.f_split_s, a.i_split_b1, a.i_split_b2} : s0;
+  const float range = SCALED ? a.f_fix_range : 8.0f;
+  bool in_range = true;  // every |g_i| < 8 * 2^k (false for an infinity or NaN)
+#pragma unroll
+  for (int i = 0; i < Q; ++i) in_range &= fabsf(g[i]) < range;
+  const Fix3 z = split3(g[0], s);
   int rH = z.H, rR = z.R, rL = z.L;
   int eH = 0, eR = 0, eL = 0, xH = 0, xR = 0, xL = 0, yH = 0, yR = 0, yL = 0;
 #pragma unroll
   for (int k = 1; k <= NPAIR; ++k) {
-    const Fix3 a = split3(g[k]), b = split3(g[k + NPAIR]);
+    const Fix3 a = split3(g[k], s), b = split3(g[k + NPAIR], s);
     const int PH = a.H + b.H, PR = a.R + b.R, PL = a.L + b.L;
     const int MH = a.H - b.H, MR = a.R - b.R, ML = a.L - b.L;
     rH += PH;
@@ -87,28 +114,32 @@ __device__ __forceinline__ FixMoments moments_fix(const float (&g)[Q]) {
       yL += rep_vy(k) * ML;
     }
   }
-  FixMoments r;
-  r.drho = join3(rH, rR, rL);
-  r.de = join3(eH, eR, eL);
-  r.jx = join3(xH, xR, xL);
-  r.jy = join3(yH, yR, yL);
+  // back from the sums of g 2^(52-k): times 2^(k-52)
+  const double back = SCALED ? a.fix_back : 1.0 / 4503599627370496.0;
+  const JT back_j = SCALED ? (JT)(sizeof(JT) == 4 ? a.f_fix_back : a.fix_back) : (JT)(1.0 / 4503599627370496.0);
+  DevMoments<JT> r;
+  r.drho = (double)join3(rH, rR, rL) * back;
+  r.de = (double)join3(eH, eR, eL) * back;
+  r.jx = (JT)join3(xH, xR, xL) * back_j;
+  r.jy = (JT)join3(yH, yR, yL) * back_j;
+  if (!in_range) r.drho = __longlong_as_double(0x7FF8000000000000LL);  // rho, and so every output, NaN
   return r;
 }
 
 // Collision of one site in the precision split described at the top of the file.
-template <class Store>
+template <bool SCALED, class Store>
 __device__ __forceinline__ void collide_site_fp32(const float (&g)[Q], const StepScalars& a, Store&& store) {
-  const FixMoments m = moments_fix(g);
+  const DevMoments<float> m = moments_fix<float, SCALED>(g, a);
   // float64: density, energy, temperature
-  const double drho = (double)m.drho * FIX_SCALE;
-  const double rho = a.rho0 + drho;  // exact: power-of-two scale
-  const double etot = fma((double)m.de, FIX_SCALE, a.rho0 * (D / C2));  // sum |v|^2 f
+  const double drho = m.drho;
+  const double rho = a.rho0 + drho;
+  const double etot = m.de + a.rho0 * (D / C2);  // sum |v|^2 f
   const float rho_f = (float)rho;
   const float r_f = __frcp_rn(rho_f);
   const double r0 = (double)r_f;
   const double inv = fma(r0, fma(-rho, r0, 1.0), r0);
   // float32: velocity c u = c^2 j / rho
-  const float c2ir_f = (float)C2 * FIX_SCALE_F * r_f;
+  const float c2ir_f = (float)C2 * r_f;
   const float Ux0 = (float)m.jx * c2ir_f, Uy0 = (float)m.jy * c2ir_f;
   const float uu = fmaf(Ux0, Ux0, Uy0 * Uy0) * (float)(1.0 / C2);
   // t = T_s - 1 = (c^2 e / rho - |u|^2) / D + tau (1 - tau) |g|^2 / D - 1: the large part in
@@ -184,7 +215,8 @@ __device__ __forceinline__ void wall_drho(const float* __restrict__ fin, int x, 
 
 
 // One warp-strip of the FP32 shifted step (see step_fp64.cuh for the strip contract).
-template <bool PERIODIC, class Ld>
+// SCALED: the lattice's reference density is 2 or more (see moments_fix).
+template <bool PERIODIC, bool SCALED, class Ld>
 __device__ __forceinline__ void step_strip_fp32(const float* __restrict__ fin, float* __restrict__ fout,
                                                 const StepScalars& a, const StepWalls& w, int x, int y0, Ld ld) {
   const int y = y0 + (threadIdx.x & 31);
@@ -220,7 +252,7 @@ __device__ __forceinline__ void step_strip_fp32(const float* __restrict__ fin, f
   }
   if (!active) return;
   const unsigned self = (unsigned)((long long)x * a.pitch + y);
-  collide_site_fp32(g, a, [&](int i, float v) { __stcs(fout + i * a.pop + self, v); });
+  collide_site_fp32<SCALED>(g, a, [&](int i, float v) { __stcs(fout + i * a.pop + self, v); });
 }
 
 }  // namespace d2q37

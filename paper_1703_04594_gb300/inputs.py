@@ -52,27 +52,30 @@ def rt_modes(lx: int, ly: int, seed: int, n_modes: int = N_MODES) -> RTModes:
                    phi=torch.tensor(phi, dtype=torch.float64))
 
 
-def interface(lx: int, ly: int, modes: RTModes) -> torch.Tensor:
-    """y_c(x) for x = 0..Lx-1."""
-    x = torch.arange(lx, dtype=torch.float64)
-    k = torch.arange(1, modes.a.numel() + 1, dtype=torch.float64)
-    arg = 2.0 * math.pi * k[None, :] * x[:, None] / lx + modes.phi[None, :]
-    return ly / 2.0 + (modes.a[None, :] * torch.cos(arg)).sum(dim=1)
+def interface(lx: int, ly: int, modes: RTModes, device=None) -> torch.Tensor:
+    """y_c(x) for x = 0..Lx-1 (on ``device``, default the modes' device)."""
+    device = device if device is not None else modes.a.device
+    x = torch.arange(lx, dtype=torch.float64, device=device)
+    k = torch.arange(1, modes.a.numel() + 1, dtype=torch.float64, device=device)
+    arg = 2.0 * math.pi * k[None, :] * x[:, None] / lx + modes.phi.to(device)[None, :]
+    return ly / 2.0 + (modes.a.to(device)[None, :] * torch.cos(arg)).sum(dim=1)
 
 
 def rt_fields(lx: int, ly: int, modes: RTModes, t_bottom: float = 1.15, t_top: float = 0.85,
-              g: float = 1e-4, width: float = INTERFACE_WIDTH):
+              g: float = 1e-4, width: float = INTERFACE_WIDTH, device=None):
     """(rho, ux, uy, T) of the hydrostatic Rayleigh-Taylor initial state, each [Lx, Ly].
 
-    ``g`` is the magnitude of gravity, which acts in -y.
+    ``g`` is the magnitude of gravity, which acts in -y.  The fields are built on ``device``
+    (default: the CPU, or the modes' device); the same operations run on any device.
     """
-    yc = interface(lx, ly, modes)                                   # [Lx]
-    y = torch.arange(ly, dtype=torch.float64)
+    yc = interface(lx, ly, modes, device)                           # [Lx]
+    device = yc.device
+    y = torch.arange(ly, dtype=torch.float64, device=device)
     T = t_bottom + (t_top - t_bottom) * 0.5 * (1.0 + torch.tanh((y[None, :] - yc[:, None]) / width))
     inv_t = 1.0 / T
     # trapezoid cumulative integral of 1/T from row 0, then re-referenced to row Ly/2
     seg = 0.5 * (inv_t[:, 1:] + inv_t[:, :-1])                      # [Lx, Ly-1]
-    cum = torch.cat([torch.zeros(lx, 1, dtype=torch.float64), torch.cumsum(seg, dim=1)], dim=1)
+    cum = torch.cat([torch.zeros(lx, 1, dtype=torch.float64, device=device), torch.cumsum(seg, dim=1)], dim=1)
     ref = ly // 2
     integral = cum - cum[:, ref:ref + 1]
     p = torch.exp(-g * integral)
@@ -81,10 +84,11 @@ def rt_fields(lx: int, ly: int, modes: RTModes, t_bottom: float = 1.15, t_top: f
     return rho, zero.clone(), zero.clone(), T
 
 
-def rt_state(lx: int, ly: int, seed: int, t_bottom: float = 1.15, t_top: float = 0.85, g: float = 1e-4):
-    """Convenience: modes drawn from ``seed`` and the resulting fields."""
+def rt_state(lx: int, ly: int, seed: int, t_bottom: float = 1.15, t_top: float = 0.85, g: float = 1e-4,
+             device=None):
+    """Convenience: modes drawn from ``seed`` and the resulting fields (on ``device``)."""
     modes = rt_modes(lx, ly, seed)
-    return rt_fields(lx, ly, modes, t_bottom=t_bottom, t_top=t_top, g=g)
+    return rt_fields(lx, ly, modes, t_bottom=t_bottom, t_top=t_top, g=g, device=device)
 
 
 def batch_workload(seed: int = 4, n: int = 256, sizes=tuple(range(128, 1025, 64)),

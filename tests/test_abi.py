@@ -132,3 +132,24 @@ def test_binding_rejects_host_tensors_and_wrong_buffers_before_any_call(lib):
     field = torch.zeros(8, 8, dtype=torch.float64)
     with pytest.raises(ValueError):
         lbm.init(p, field, field, field, field, host_state)
+
+
+def test_batch_plan_rejects_buffers_shared_between_lattices(lib):
+    """lbm_batch_plan checks the 2n state buffers of a batch against each other before any
+    CUDA call: one lattice's buffer overlapping another lattice's is LBM_EINVAL (the fake
+    addresses are never touched)."""
+    ps = [lbm.Params(8, 8), lbm.Params(16, 8)]
+    arr = (lbm.CParams * 2)(*[p.c() for p in ps])
+    nb = [lbm.buffer_bytes(p) for p in ps]
+    base = 1 << 36
+
+    def plan(a0, b0, a1, b1):
+        pa = (ctypes.c_void_p * 2)(a0, a1)
+        pb = (ctypes.c_void_p * 2)(b0, b1)
+        h = ctypes.c_void_p()
+        return lib.lbm_batch_plan(arr, pa, pb, 2, ctypes.byref(h))
+
+    step = 1 << 24                               # far apart: 16 MiB between buffers
+    assert plan(base, base + 2 * step, base + 2 * step + nb[0] // 2, base + 3 * step) == lbm.EINVAL
+    assert plan(base, base + step, base + 2 * step, base) == lbm.EINVAL          # shared buffer
+    assert plan(base + step, base, base + 2 * step, base + step + 256) == lbm.EINVAL

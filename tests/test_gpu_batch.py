@@ -1,8 +1,9 @@
 """Batched stepping of independent lattices of uneven sizes (C-ABI lbm_batch_*).
 
-Every mode runs the same per-strip step as the single-lattice kernel, so each lattice of a
-batch must equal lbm_run on that lattice bit for bit (FP64, FP64 with the fixed-point
-relaxation, and FP32 storage).  The
+Each lattice of a batch is checked against the oracle run of that lattice alone (the
+parity bars of its form).  Every mode also runs the same per-strip step as the
+single-lattice kernel, so each lattice must equal lbm_run on that lattice bit for bit (FP64,
+FP64 with the fixed-point relaxation, and FP32 storage).  The
 persistent mode's grid barrier is bounded in time: a test makes the wait expire (a
 barrier that waits for a block that never arrives) and checks the reported status and
 that the GPU context stays usable.
@@ -10,8 +11,9 @@ that the GPU context stays usable.
 import pytest
 import torch
 
+from oracle import lbm as OL
 from paper_1703_04594_gb300 import lbm
-from tests.gpu_util import require_gpu, rt_fields
+from tests.gpu_util import field_errors, oracle_params, rel_err, require_gpu, rt_fields, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -23,17 +25,19 @@ def _gpu():
     require_gpu()
 
 
-def make_batch(precision, bc=lbm.BC_WALLS, seed0=100):
-    params, fa, fb = [], [], []
+def make_batch(precision, bc=lbm.BC_WALLS, seed0=100, with_fields=False):
+    params, fa, fb, fields = [], [], [], []
     for j, (lx, ly, tau) in enumerate(SHAPES):
         p = lbm.Params(lx, ly, tau=tau, gx=1e-4 * (j % 2), precision=precision, bc=bc)
-        dev = [t.contiguous().cuda() for t in rt_fields(p, seed0 + j)]
+        fl = rt_fields(p, seed0 + j)
+        dev = [t.contiguous().cuda() for t in fl]
         a, b = lbm.empty_state(p), lbm.empty_state(p)
         lbm.init(p, *dev, a)
         params.append(p)
         fa.append(a)
         fb.append(b)
-    return params, fa, fb
+        fields.append(fl)
+    return (params, fa, fb, fields) if with_fields else (params, fa, fb)
 
 
 def reference(params, fa, steps):
@@ -63,6 +67,33 @@ def test_batch_equals_single_lattice_runs(precision, mode, tx):
     assert b.status() == lbm.OK
     assert b.parity() == 1
     assert_equal_states(params, b.states(), want)
+    b.close()
+
+
+ORACLE_STEPS = 5
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP64_FIXED, lbm.FP32_SHIFTED])
+@pytest.mark.parametrize("mode", [lbm.BATCH_PER_STEP, lbm.BATCH_PERSISTENT])
+@pytest.mark.parametrize("bc", [lbm.BC_WALLS, lbm.BC_PERIODIC_Y])
+def test_batch_matches_oracle(precision, mode, bc):
+    """Every lattice of a batch against the oracle run of that lattice alone (its own size,
+    tau, gravity and interface): populations within 1e-12 relative after 5 steps for the
+    float64 forms; the FP32 form's per-field bar (density and temperature max and RMS
+    relative, velocity relative to the sound speed) within 1e-5."""
+    params, fa, fb, fields = make_batch(precision, bc=bc, seed0=600, with_fields=True)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(mode, 4)
+    b.run(ORACLE_STEPS)
+    torch.cuda.synchronize()
+    assert b.status() == lbm.OK
+    for p, got, fl in zip(params, b.states(), fields):
+        want = OL.run(OL.init_equilibrium(*fl), oracle_params(p), ORACLE_STEPS)
+        if precision == lbm.FP32_SHIFTED:
+            err = field_errors([t.cpu() for t in lbm.moments(p, got)], OL.fields(want))
+            assert max(err[k] for k in ("rho_max", "rho_rms", "T_max", "T_rms", "u_max_cs")) <= 1e-5, (p, err)
+        else:
+            assert rel_err(to_host(p, got), want) <= 1e-12, p
     b.close()
 
 
@@ -136,6 +167,23 @@ def test_barrier_wait_expires_and_reports_timeout():
     b.close()
 
 
+def test_timeout_of_an_earlier_run_is_not_erased_by_a_later_one():
+    """Two persistent runs queued before the status is read: the first one's barrier wait
+    expires (a block that never arrives), the second one runs normally.  The status still
+    reports the first run's timeout, once."""
+    params, fa, fb = make_batch(lbm.FP64, seed0=450)
+    b = lbm.Batch(params, fa, fb)
+    b.configure(lbm.BATCH_PERSISTENT, 4)
+    b.set_wait(timeout_ns=200_000_000, phantom_arrivals=1)
+    b.run(3)
+    b.set_wait(timeout_ns=2_000_000_000, phantom_arrivals=0)
+    b.run(3)
+    torch.cuda.synchronize()
+    assert b.status() == lbm.ETIMEOUT
+    assert b.status() == lbm.OK
+    b.close()
+
+
 def test_plan_rejects_mixed_precision_and_aliasing():
     params, fa, fb = make_batch(lbm.FP64)
     bad = list(params)
@@ -144,3 +192,5 @@ def test_plan_rejects_mixed_precision_and_aliasing():
         lbm.Batch(bad, fa, fb)
     with pytest.raises(lbm.LbmError):
         lbm.Batch(params, fa, fa)                             # f_a == f_b
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch([params[0], params[0]], [fa[0], fb[0]], [fb[1], fa[0]])   # one buffer in two lattices

@@ -1,13 +1,16 @@
 """AoS, partitioned-SoA and CAoSoA layouts of the fused FP64 step (the paper's layout
-comparison, Sec. 4) give the SoA step's results: the same arithmetic on the same gathered
-values, with different addresses.  The compiler may contract multiply-adds differently in each kernel,
-so the bar is 1e-13 relative after 3 steps (the single-collide bar), not bit equality;
+comparison, Sec. 4; thermal walls only).  Each layout's step is checked against the oracle
+(populations within 1e-12 relative after 3 steps, the float64 parity bar).  It
+also gives the SoA step's results: the same arithmetic on the same gathered values, with
+different addresses.  The compiler may contract multiply-adds differently in each kernel,
+so that bar is 1e-13 relative after 3 steps (the single-collide bar), not bit equality;
 the layout conversions themselves are exact."""
 import pytest
 import torch
 
+from oracle import lbm as OL
 from paper_1703_04594_gb300 import lbm
-from tests.gpu_util import device_init, require_gpu, rt_fields
+from tests.gpu_util import device_init, oracle_params, rel_err, require_gpu, rt_fields, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +34,26 @@ def test_layout_step_equals_soa(layout, lx, ly):
     back = lbm.convert_layout(p, a, layout, torch.zeros_like(f), lbm.LAYOUT_SOA)
     g, w = back[:, :, :ly], want[:, :, :ly]
     assert float(((g - w).abs() / w.abs()).max()) <= 1e-13
+
+
+def layout_run(p, f, layout, steps):
+    a = lbm.convert_layout(p, f, lbm.LAYOUT_SOA, torch.zeros_like(f), layout)
+    b = torch.zeros_like(f)
+    for _ in range(steps):
+        lbm.step_layout(p, layout, a, b)
+        a, b = b, a
+    return lbm.convert_layout(p, a, layout, torch.zeros_like(f), lbm.LAYOUT_SOA)
+
+
+@pytest.mark.parametrize("layout", [lbm.LAYOUT_AOS, lbm.LAYOUT_PSOA, lbm.LAYOUT_CAOSOA])
+@pytest.mark.parametrize("lx,ly", [(37, 45), (64, 128), (6, 33)])
+def test_layout_step_matches_oracle(layout, lx, ly):
+    p = lbm.Params(lx, ly, tau=0.7, gx=1e-4)
+    fields = rt_fields(p, seed=23)
+    fields = (fields[0], fields[1] + 0.01, fields[2] - 0.005, fields[3])   # moving fluid
+    got = layout_run(p, device_init(p, fields), layout, 3)
+    want = OL.run(OL.init_equilibrium(*fields), oracle_params(p), 3)
+    assert rel_err(to_host(p, got), want) <= 1e-12
 
 
 @pytest.mark.parametrize("layout", [lbm.LAYOUT_AOS, lbm.LAYOUT_PSOA, lbm.LAYOUT_CAOSOA])
