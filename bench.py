@@ -81,8 +81,9 @@ def _args():
     ap.add_argument("--variant", choices=["fused", "separate", "push", "aos", "psoa", "caosoa"], default="fused",
                     help="fused SoA step; separate propagate/bc/collide kernels with the pull or push "
                          "propagate; fused step in the AoS, partitioned-SoA or CAoSoA layout (FP64)")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "fp64fix"], default="fp64",
-                    help="fp32 = FP32 shifted-deviation storage (fused only); fp64fix = float64 storage "
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32c", "fp64fix"], default="fp64",
+                    help="fp32 = FP32 shifted-deviation storage (fused only); fp32c = the same storage with "
+                         "the conserved-moment correction; fp64fix = float64 storage "
                          "with the fixed-point relaxation (fused only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed", action="store_true",
@@ -92,10 +93,11 @@ def _args():
     ap.add_argument("--batch-kind", choices=["uneven", "small"], default="uneven",
                     help="uneven = 256 lattices, Lx in 128..1024, Ly = 2 Lx; small = 1024 lattices, "
                          "Lx in 32..128 (a launch-bound batch)")
-    ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "adjoint", "adjoint-step"], default="single",
                     help="batch = 256 independent lattices of uneven sizes; adjoint = gradient of the "
-                         "kinetic energy after 500 steps of a 512x1024 lattice (checkpoints every 22)")
-    ap.add_argument("--batch-n", type=int, default=256)
+                         "kinetic energy after 500 steps of a 512x1024 lattice (checkpoints every 22); "
+                         "adjoint-step = the adjoint step kernel alone on --lx x --ly (default 512x1024)")
+    ap.add_argument("--batch-n", type=int, default=0, help="lattices of the batch (default 256, or 1024 small)")
     ap.add_argument("--lx", type=int, default=LX, help="lattice width (profiling of smaller cases)")
     ap.add_argument("--ly", type=int, default=LY, help="lattice height (profiling of smaller cases)")
     return ap.parse_args()
@@ -231,12 +233,11 @@ def run_ours(a):
         raise RuntimeError("CUDA library missing: run __graft_entry__.build() first")
 
     lx, ly = a.lx, a.ly
-    fp32 = a.precision == "fp32"
+    fp32 = a.precision in ("fp32", "fp32c")
     fix = a.precision == "fp64fix"
     if (fp32 or fix) and a.variant != "fused":
         raise SystemExit(f"--precision {a.precision} supports the fused step only")
-    p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
-                   precision=lbm.FP32_SHIFTED if fp32 else (lbm.FP64_FIXED if fix else lbm.FP64))
+    p = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP, precision=prec_enum(lbm, a.precision))
     sites = lx * ly
     dev = [t.contiguous() for t in I.rt_state(lx, ly, SEED + rank, t_bottom=T_BOTTOM, t_top=T_TOP, g=abs(GY),
                                               device="cuda")]
@@ -387,6 +388,7 @@ def run_ours(a):
         del bufs, fa, fb, ftmp
         torch.cuda.empty_cache()
         forms["fp32"] = single_form(a, "fp32", dev)
+        forms["fp32_conserved"] = single_form(a, "fp32c", dev)
         del dev
         torch.cuda.empty_cache()
         forms["batch_fp64"] = batch_form(a, "fp64")
@@ -419,6 +421,14 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+DTYPE = {"fp32": "f32+i64+f64", "fp32c": "f32+i64+f64", "fp64fix": "f64+i64", "fp64": "f64"}
+
+
+def prec_enum(lbm, precision):
+    return {"fp32": lbm.FP32_SHIFTED, "fp32c": lbm.FP32_CONSERVED, "fp64fix": lbm.FP64_FIXED,
+            "fp64": lbm.FP64}[precision]
+
+
 def kernel_roofline(bound, work_per_site, sites, ms, kernel, traffic=None):
     """Roofline record of one kernel: algorithmic bytes (hbm) or flops (alu) per launch over
     its CUDA-event time, against the measured HBM copy rate or the FP64 unit-count peak."""
@@ -441,7 +451,8 @@ def single_form(a, precision, dev_fields):
     from paper_1703_04594_gb300 import lbm
 
     p = lbm.Params(LX, LY, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP,
-                   precision={"fp32": lbm.FP32_SHIFTED, "fp64fix": lbm.FP64_FIXED}[precision])
+                   precision={"fp32": lbm.FP32_SHIFTED, "fp32c": lbm.FP32_CONSERVED,
+                              "fp64fix": lbm.FP64_FIXED}[precision])
     bufs = [lbm.empty_state(p), lbm.empty_state(p)]
     lbm.init(p, *dev_fields, bufs[0])
     stream = torch.cuda.current_stream()
@@ -457,13 +468,13 @@ def single_form(a, precision, dev_fields):
         torch.cuda.synchronize()
     ms = ev[0].elapsed_time(ev[1]) / a.steps
     sites = LX * LY
-    fp32 = precision == "fp32"
+    fp32 = precision in ("fp32", "fp32c")
+    kernel = {"fp32": "k_step_fp32", "fp32c": "k_step_fp32 (conserved moments)", "fp64fix": "k_step_fix64"}[precision]
     out = {"value": sites / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": a.steps,
            "dtype": "f32+i64+f64" if fp32 else "f64+i64",
            "workload": f"{LX}x{LY} RT lattice, seed {SEED}",
            "roofline": kernel_roofline("hbm", BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64, sites, ms,
-                                       "k_step_fp32" if fp32 else "k_step_fix64",
-                                       TRAFFIC_BYTES_PER_LAUNCH.get(precision)),
+                                       kernel, TRAFFIC_BYTES_PER_LAUNCH.get(precision)),
            "gpu_launches": a.steps, "clocks": clk.summary()}
     del bufs
     torch.cuda.empty_cache()
@@ -488,7 +499,7 @@ def build_batch(kind, n, seed, precision):
     from paper_1703_04594_gb300 import inputs as I
     from paper_1703_04594_gb300 import lbm
 
-    prec = {"fp32": lbm.FP32_SHIFTED, "fp64fix": lbm.FP64_FIXED, "fp64": lbm.FP64}[precision]
+    prec = prec_enum(lbm, precision)
     spec = batch_lattices(kind, n, seed)
     params, fa, fb = [], [], []
     for lx, ly, tau, s in spec:
@@ -551,11 +562,11 @@ def time_batch(b, mode_cfg, steps, warmup, graph=False):
 def batch_roofline(precision, sites, ms_step, cfg):
     from paper_1703_04594_gb300 import lbm
 
-    kname = {"fp32": "fp32", "fp64fix": "fix64", "fp64": "double"}[precision]
+    kname = {"fp32": "fp32", "fp32c": "fp32 conserved", "fp64fix": "fix64", "fp64": "double"}[precision]
     kernel = ("k_batch_persistent<" if cfg["mode"] == lbm.BATCH_PERSISTENT else "k_batch_step<") + kname + ">"
     if precision == "fp64":
         return kernel_roofline("alu", FLOPS_PER_SITE_FP64, sites, ms_step, kernel)
-    return kernel_roofline("hbm", BYTES_PER_SITE_FP32 if precision == "fp32" else BYTES_PER_SITE_FP64, sites,
+    return kernel_roofline("hbm", BYTES_PER_SITE_FP32 if precision in ("fp32", "fp32c") else BYTES_PER_SITE_FP64, sites,
                            ms_step, kernel)
 
 
@@ -574,7 +585,7 @@ def batch_form(a, precision, kind="uneven", n=None, seed=4):
         ms = time_batch(b, tuned, a.steps, a.warmup)
     ms_loop = time_batch(b, (lbm.BATCH_LOOP, 4, 0), a.steps, a.warmup)
     out = {"value": sites * a.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / a.steps,
-           "steps": a.steps, "dtype": {"fp32": "f32+i64+f64", "fp64fix": "f64+i64", "fp64": "f64"}[precision],
+           "steps": a.steps, "dtype": DTYPE[precision],
            "workload": (f"{len(spec)} RT lattices, " +
                         ("Lx in 32..128" if kind == "small" else "Lx in 128..1024") + ", Ly = 2 Lx, tau in [0.6, 1.0]"),
            "sites": sites, "autotuned": cfg,
@@ -599,8 +610,8 @@ def run_batch(a):
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
-    b, spec, params, fa, fb, cfg = build_batch(a.batch_kind, a.batch_n if a.batch_kind == "uneven" else 1024,
-                                               4 + rank, a.precision)
+    n = a.batch_n or (256 if a.batch_kind == "uneven" else 1024)
+    b, spec, params, fa, fb, cfg = build_batch(a.batch_kind, n, 4 + rank, a.precision)
     sites = b.sites()
     tuned = (cfg["mode"], cfg["tile_columns"], cfg["blocks_per_sm"])
     with ClockSampler(local) as clk:
@@ -617,7 +628,7 @@ def run_batch(a):
         line = {"metric": "D2Q37 MLUPS (batched)", "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp32": "f32+i64+f64", "fp64fix": "f64+i64", "fp64": "f64"}[a.precision],
+                "dtype": DTYPE[a.precision],
                 "data": "synthetic",
                 "config": {"workload": f"{len(spec)} RT lattices ({a.batch_kind}), Ly = 2 Lx, tau in [0.6, 1.0]",
                            "sites": sites, "precision": a.precision, "autotuned": cfg,
@@ -635,6 +646,59 @@ ADJ_LX, ADJ_LY, ADJ_N, ADJ_EVERY = 512, 1024, 500, 22
 # algorithmic bytes per site of one adjoint step: the gathered f~ (37 x 8), lambda^{n+1}
 # read (37 x 8) and lambda^n written (37 x 8)
 BYTES_PER_SITE_ADJ = 888
+
+
+def adjoint_step_ms(lx, ly, modes, warmup, calls):
+    """The adjoint step alone (collide VJP with the transposed propagate as its store, wall
+    slots, tau partials): CUDA events over back-to-back calls on a mid-run RT state (100
+    steps in).  Returns (ms per call, clock summary)."""
+    import torch
+
+    from paper_1703_04594_gb300 import inputs as I
+    from paper_1703_04594_gb300 import lbm
+
+    p64 = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
+    fields = [t.contiguous() for t in I.rt_fields(lx, ly, modes, T_BOTTOM, T_TOP, abs(GY), device="cuda")]
+    f = lbm.empty_state(p64)
+    lbm.init(p64, *fields, f)
+    f = lbm.run(p64, f, lbm.empty_state(p64), 100).clone()
+    lam = [lbm.empty_state(p64), lbm.empty_state(p64)]
+    lbm.kinetic_energy_grad(p64, f, lam[0])
+    work = lbm.adjoint_work(p64)
+    dtau = torch.zeros((), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(warmup):
+        lbm.adjoint_step(p64, f, lam[k % 2], lam[(k + 1) % 2], dtau, work, stream)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(0) as aclk:
+        ev[0].record(stream)
+        for k in range(calls):
+            lbm.adjoint_step(p64, f, lam[(warmup + k) % 2], lam[(warmup + k + 1) % 2], dtau, work, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / calls, aclk.summary()
+
+
+def run_adjoint_step(a):
+    """The adjoint step kernel alone on an --lx x --ly RT lattice (default 512 x 1024): one
+    JSON line with its time and HBM roofline (the profiling target of the adjoint)."""
+    import torch
+
+    from paper_1703_04594_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    lx, ly = (a.lx, a.ly) if (a.lx, a.ly) != (LX, LY) else (ADJ_LX, ADJ_LY)
+    ms, clk = adjoint_step_ms(lx, ly, I.rt_modes(lx, ly, 5), warmup=a.warmup, calls=a.steps)
+    sites = lx * ly
+    print(json.dumps({"metric": "D2Q37 adjoint step MLUPS", "value": sites / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                      "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f64+i64", "data": "synthetic",
+                      "config": {"workload": f"lbm_adjoint_step on a {lx}x{ly} RT state"},
+                      "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms,
+                                                  "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
+                                                  TRAFFIC_BYTES_PER_LAUNCH.get("adjoint")),
+                      "clocks": clk}), flush=True)
 
 
 def adjoint_form(a, repeats, precision="fp64", seed=5):
@@ -681,29 +745,7 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
             gradient()
         torch.cuda.synchronize()
         t_grad = (time.perf_counter() - t0) / repeats
-    # the adjoint step alone (collide VJP with the transposed propagate, wall slots, tau
-    # partials): CUDA events over back-to-back calls on a mid-run state
-    p64 = lbm.Params(lx, ly, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
-    fields = [t.contiguous().cuda() for t in I.rt_fields(lx, ly, modes, T_BOTTOM, T_TOP, abs(GY))]
-    f = lbm.empty_state(p64)
-    lbm.init(p64, *fields, f)
-    f = lbm.run(p64, f, lbm.empty_state(p64), 100).clone()
-    lam = [lbm.empty_state(p64), lbm.empty_state(p64)]
-    lbm.kinetic_energy_grad(p64, f, lam[0])
-    work = lbm.adjoint_work(p64)
-    dtau = torch.zeros((), dtype=torch.float64, device="cuda")
-    stream = torch.cuda.current_stream()
-    for k in range(4):
-        lbm.adjoint_step(p64, f, lam[k % 2], lam[(k + 1) % 2], dtau, work, stream)
-    calls = 40
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with ClockSampler(0) as aclk:
-        ev[0].record(stream)
-        for k in range(calls):
-            lbm.adjoint_step(p64, f, lam[k % 2], lam[(k + 1) % 2], dtau, work, stream)
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-    ms_adj = ev[0].elapsed_time(ev[1]) / calls
+    ms_adj, aclk = adjoint_step_ms(lx, ly, modes, warmup=4, calls=40)
     sites = lx * ly
     return {"value": whole_job_mlups(sites, n, 1, t_grad * 1e3), "unit": "MLUPS",
             "what": "MLUPS of the whole gradient: forward run with checkpoints, then recomputation and the "
@@ -718,7 +760,7 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
             "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms_adj,
                                         "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
                                         TRAFFIC_BYTES_PER_LAUNCH.get("adjoint")),
-            "clocks": clk.summary(), "adjoint_step_clocks": aclk.summary()}
+            "clocks": clk.summary(), "adjoint_step_clocks": aclk}
 
 
 def run_adjoint(a):
@@ -750,6 +792,8 @@ def main():
         run_batch(a)
     elif a.workload == "adjoint":
         run_adjoint(a)
+    elif a.workload == "adjoint-step":
+        run_adjoint_step(a)
     else:
         run_ours(a)
 

@@ -19,7 +19,7 @@
  * Layout (structure of arrays, Sec. 4, "SoA"; y contiguous, two copies read and written
  * alternately): population i of site (x, y) is element  i*lx*pitch + x*pitch + y  of a
  * state buffer.  pitch = lbm_pitch(p) >= ly; elements y >= ly of a column are padding and
- * are never read.  FP64 and FP64_FIXED states hold double f_i.  FP32_SHIFTED states hold float
+ * are never read.  FP64 and FP64_FIXED states hold double f_i.  FP32_SHIFTED and FP32_CONSERVED states hold float
  * (f_i - w_i * rho0).  Population order: 0 = rest, 1..18 = the vectors returned by
  * lbm_model in that order, 18 + k = -(vector k).
  *
@@ -60,7 +60,13 @@ enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, L
  * in a stated physical range (float64 elsewhere).  lbm_step, lbm_run, lbm_init, lbm_moments,
  * lbm_kinetic_energy*, lbm_simulate_host and the batch entry points accept it; the separate
  * kernels, layouts and adjoint entry points take LBM_FP64 (its states are the same). */
-enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_FIXED = 2 };
+/* LBM_FP32_CONSERVED: the FP32_SHIFTED storage (same buffers, interchangeable states) with a
+ * collision that restores the exact post-collision mass and energy of every site after its
+ * float32 arithmetic (a second moment sum over the outputs and a correction along the even
+ * first Hermite polynomials): float32 rounding then no longer accumulates as pressure noise
+ * in the conserved fields, which is what limits the velocity accuracy of long FP32_SHIFTED
+ * runs.  Accepted wherever LBM_FP32_SHIFTED is. */
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_FIXED = 2, LBM_FP32_CONSERVED = 3 };
 enum lbm_bc { LBM_BC_WALLS = 0, LBM_BC_PERIODIC_Y = 1 /* test mode: y wraps like x */ };
 
 /* Problem parameters, as the paper states the problem (Sec. 3): lattice size, BGK
@@ -216,7 +222,7 @@ int32_t lbm_init_adjoint(const lbm_params* p, const double* rho_dev, const doubl
  * The paper steps one lattice per process; this runs many independent problems in one
  * launch so that small lattices fill the GPU (its start-up mini-benchmark tuning, Sec. 6,
  * becomes the autotuner below).  All lattices of a batch share precision (LBM_FP64,
- * LBM_FP64_FIXED or LBM_FP32_SHIFTED) and bc mode; each has its own lbm_params and its own
+ * LBM_FP64_FIXED, LBM_FP32_SHIFTED or LBM_FP32_CONSERVED) and bc mode; each has its own lbm_params and its own
  * two state buffers.  Results are bit-identical to lbm_run on each lattice. */
 typedef struct lbm_batch lbm_batch;
 enum lbm_batch_mode {
@@ -227,8 +233,9 @@ enum lbm_batch_mode {
 /* Validates n lattices and binds their buffers (f_a_dev[j], f_b_dev[j]: device states of
  * lbm_buffer_bytes(&params[j]) bytes, current state in f_a; no two of the 2n buffers may
  * overlap, else LBM_EINVAL).  Allocates the batch's own
- * device descriptor table, tile table and barrier word (freed by lbm_batch_destroy).  Synchronous.  Default configuration: persistent, tiles of 32 x 4,
- * as many blocks per SM as fit.  At most 65535 lattices. */
+ * device descriptor table, tile table and barrier word (freed by lbm_batch_destroy).
+ * Synchronous.  Default configuration: one launch per step, tiles of 32 x 4.  At most 65535
+ * lattices. */
 int32_t lbm_batch_plan(const lbm_params* params, void* const* f_a_dev, void* const* f_b_dev, int32_t n,
                        lbm_batch** out);
 /* Sets mode, tile shape (a block steps a tile of 32 rows x tile_columns columns, one warp
@@ -238,7 +245,10 @@ int32_t lbm_batch_configure(lbm_batch* b, int32_t mode, int32_t tile_columns, in
 /* Reads the configuration (blocks_per_sm: the value the persistent launch uses, else 0). */
 int32_t lbm_batch_config(const lbm_batch* b, int32_t* mode, int32_t* tile_columns, int32_t* blocks_per_sm);
 /* Times every candidate configuration for trial_steps steps (after one warm-up step each)
- * and keeps the fastest.  It ADVANCES the batch by (trial_steps + 1) steps per candidate:
+ * and keeps the fastest.  Candidates: per-step launches with tiles of 2, 4 and 8 columns;
+ * for batches of at most 2^20 sites also the persistent launch with those tiles and the
+ * two largest block counts per SM (on larger batches its L1-bypassing loads cost more
+ * than the kernel boundaries it saves).  It ADVANCES the batch by (trial_steps + 1) steps per candidate:
  * call it before initialising the states, or on states whose evolution does not matter.
  * Synchronous. */
 int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream);

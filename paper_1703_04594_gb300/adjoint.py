@@ -14,10 +14,13 @@ the adjoint steps are the FP64 ones either way.
 
 Memory: the forward pass keeps a checkpoint every ``every`` steps (default ceil(sqrt(N)));
 the backward pass recomputes each segment's states from its checkpoint, newest segment
-first, and walks the adjoint back through it.  Peak: ceil(N/every) + every + 3 states.
+first, and walks the adjoint back through it.  On a GPU the recomputation of the next
+(earlier) segment runs on a second stream while the adjoint steps of the current one run,
+so the two kernels share the SMs.  Peak: ceil(N/every) + 2 every + 3 states.
 """
 from __future__ import annotations
 
+import contextlib
 import dataclasses
 import math
 
@@ -64,14 +67,37 @@ class _KineticEnergyAfter(torch.autograd.Function):
         lam_other = lbm.empty_state(pa, dev)
         dtau = torch.zeros((), dtype=torch.float64, device=dev)
         work = lbm.adjoint_work(pa, dev)
-        starts = sorted(ctx.checkpoints)
-        for k in reversed(starts):
+        order = sorted(ctx.checkpoints, reverse=True)      # newest segment first
+        cuda = dev.type == "cuda"
+        main = torch.cuda.current_stream(dev) if cuda else None
+        side = torch.cuda.Stream(dev) if cuda else None
+        if cuda:
+            side.wait_stream(main)                         # the checkpoints are ready
+
+        def recompute(k):
+            """f^k .. f^{end-1} of the segment starting at checkpoint k (on the side stream)."""
             end = min(k + every, n_steps)
-            states = [ctx.checkpoints[k]]
-            for _ in range(k, end - 1):                    # recompute f^{k+1} .. f^{end-1}
-                nxt = lbm.empty_state(p, dev)
-                lbm.step(p, states[-1], nxt)
-                states.append(nxt)
+            with torch.cuda.stream(side) if cuda else contextlib.nullcontext():
+                states = [ctx.checkpoints[k]]
+                for _ in range(k, end - 1):
+                    nxt = lbm.empty_state(p, dev)
+                    lbm.step(p, states[-1], nxt)
+                    states.append(nxt)
+                done = None
+                if cuda:
+                    done = torch.cuda.Event()
+                    done.record(side)
+            return k, end, states, done
+
+        pending = recompute(order[0])
+        for idx in range(len(order)):
+            k, end, states, done = pending
+            if cuda:
+                main.wait_event(done)
+                for t in states:                           # read on the main stream below
+                    t.record_stream(main)
+            if idx + 1 < len(order):
+                pending = recompute(order[idx + 1])        # overlaps the adjoint steps below
             for n in reversed(range(k, end)):
                 lbm.adjoint_step(pa, states[n - k], lam, lam_other, dtau, work)
                 lam, lam_other = lam_other, lam

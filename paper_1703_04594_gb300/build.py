@@ -30,7 +30,9 @@ def nvcc() -> str:
 
 
 def _compile(src: str, obj: str) -> str:
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    # LBM_NVCC_DEFINES: extra "-DNAME=VALUE" flags (launch-bound and unroll tuning knobs)
+    extra = os.environ.get("LBM_NVCC_DEFINES", "").split()
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{res.stdout}\n{res.stderr}")

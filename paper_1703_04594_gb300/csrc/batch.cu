@@ -58,8 +58,10 @@ namespace {
 
 // Step kinds: the strip functions of the three storage/arithmetic forms.
 // kFp32Scaled: FP32 storage where some lattice has a reference density of 2 or more (the
-// moment sums read each lattice's scale constants; see step_fp32.cuh).
-enum BatchKind { kFp64 = 0, kFp32 = 1, kFix64 = 2, kFp32Scaled = 3 };
+// moment sums read each lattice's scale constants; see step_fp32.cuh); kFp32Cons and
+// kFp32ConsScaled: the same with the conserved-moment correction (LBM_FP32_CONSERVED).
+enum BatchKind { kFp64 = 0, kFp32 = 1, kFix64 = 2, kFp32Scaled = 3, kFp32Cons = 4, kFp32ConsScaled = 5 };
+constexpr bool kind_fp32(int k) { return k == kFp32 || k == kFp32Scaled || k == kFp32Cons || k == kFp32ConsScaled; }
 
 template <int K>
 struct KindOf {
@@ -71,6 +73,14 @@ struct KindOf<kFp32> {
 };
 template <>
 struct KindOf<kFp32Scaled> {
+  using T = float;
+};
+template <>
+struct KindOf<kFp32Cons> {
+  using T = float;
+};
+template <>
+struct KindOf<kFp32ConsScaled> {
   using T = float;
 };
 
@@ -98,7 +108,9 @@ __device__ __forceinline__ void batch_tile(const BatchLattice* __restrict__ L, c
   if constexpr (KIND == kFp64) step_strip_fp64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld);
   else if constexpr (KIND == kFix64)
     step_strip_fix64<PERIODIC>(src, dst, B.a, B.a, x, ty * 32, ld, staged + threadIdx.y * (Q * 32));
-  else step_strip_fp32<PERIODIC, KIND == kFp32Scaled>(src, dst, B.a, B.a, x, ty * 32, ld);
+  else
+    step_strip_fp32<PERIODIC, KIND == kFp32Scaled || KIND == kFp32ConsScaled, KIND == kFp32Cons || KIND == kFp32ConsScaled>(
+        src, dst, B.a, B.a, x, ty * 32, ld);
 }
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -148,9 +160,11 @@ __device__ __forceinline__ bool grid_barrier(BatchSync* sync, unsigned target, l
 
 // Register caps, with at most 256 threads per block (8 warps): the FP32 step keeps three
 // such blocks resident per SM (80 registers), the float64 step two (128 registers, as its
-// single-lattice kernel), the fixed-point FP64 step the 96 registers of its single-lattice
-// kernel (5 blocks of 4 warps per SM, which its shared staging also allows).
-constexpr int batch_max_regs(int kind) { return kind == kFp64 ? 128 : (kind == kFix64 ? 96 : 80); }
+// single-lattice kernel), the fixed-point FP64 step and the conserved-moment FP32 step the
+// 96 registers of their single-lattice kernels (5 blocks of 4 warps per SM).
+constexpr int batch_max_regs(int kind) {
+  return kind == kFp64 ? 128 : (kind == kFix64 || kind == kFp32Cons || kind == kFp32ConsScaled ? 96 : 80);
+}
 
 extern __shared__ double batch_staged[];
 
@@ -192,7 +206,7 @@ struct lbm_batch {
   BatchLattice* dev_lattices = nullptr;
   BatchSync* dev_sync = nullptr;
   int parity = 0;
-  int mode = LBM_BATCH_PERSISTENT;
+  int mode = LBM_BATCH_PER_STEP;
   int warps_per_block = 4;  // = tile width TX
   int blocks_per_sm = 0;  // 0 = as many as fit
   long long timeout_ns = 2000000000LL;
@@ -213,6 +227,7 @@ int32_t cuda_status(cudaError_t e) {
 
 int kind_of(const lbm_batch* b) {
   if (b->precision == LBM_FP32_SHIFTED) return b->fp32_scaled ? kFp32Scaled : kFp32;
+  if (b->precision == LBM_FP32_CONSERVED) return b->fp32_scaled ? kFp32ConsScaled : kFp32Cons;
   return b->precision == LBM_FP64_FIXED ? kFix64 : kFp64;
 }
 
@@ -230,6 +245,8 @@ void* persistent_kernel(const lbm_batch* b) {
     case kFix64: return persistent_fn<kFix64>(b->periodic);
     case kFp32: return persistent_fn<kFp32>(b->periodic);
     case kFp32Scaled: return persistent_fn<kFp32Scaled>(b->periodic);
+    case kFp32Cons: return persistent_fn<kFp32Cons>(b->periodic);
+    case kFp32ConsScaled: return persistent_fn<kFp32ConsScaled>(b->periodic);
     default: return persistent_fn<kFp64>(b->periodic);
   }
 }
@@ -238,6 +255,8 @@ void* per_step_kernel(const lbm_batch* b) {
     case kFix64: return per_step_fn<kFix64>(b->periodic);
     case kFp32: return per_step_fn<kFp32>(b->periodic);
     case kFp32Scaled: return per_step_fn<kFp32Scaled>(b->periodic);
+    case kFp32Cons: return per_step_fn<kFp32Cons>(b->periodic);
+    case kFp32ConsScaled: return per_step_fn<kFp32ConsScaled>(b->periodic);
     default: return per_step_fn<kFp64>(b->periodic);
   }
 }
@@ -475,6 +494,9 @@ int32_t lbm_batch_run(lbm_batch* b, int32_t n_steps, void* stream) {
   return run(b, n_steps, (cudaStream_t)stream);
 }
 
+// Batches up to this many sites also try the persistent launch when autotuning.
+constexpr int64_t kPersistentCandidateSites = 1 << 20;
+
 int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream) {
   if (!b || trial_steps < 1) return LBM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -483,9 +505,15 @@ int32_t lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, void* stream) {
   };
   std::vector<Cand> cands;
   for (int tx : {2, 4, 8}) cands.push_back({LBM_BATCH_PER_STEP, tx, 0});
-  for (int tx : {2, 4, 8}) {
-    const int fit = max_blocks_per_sm(b, tx);
-    for (int bps = fit; bps >= 1 && bps >= fit - 1; --bps) cands.push_back({LBM_BATCH_PERSISTENT, tx, bps});
+  // The persistent launch saves one kernel boundary per step (a few microseconds) but its
+  // loads must bypass L1 (other SMs rewrite the buffers between steps), which measured
+  // 7 % (float64) to 32 % (FP32) slower per step on batches of millions of sites.  It is
+  // a candidate only where a step is short enough for the boundary to matter.
+  if (lbm_batch_sites(b) <= kPersistentCandidateSites) {
+    for (int tx : {2, 4, 8}) {
+      const int fit = max_blocks_per_sm(b, tx);
+      for (int bps = fit; bps >= 1 && bps >= fit - 1; --bps) cands.push_back({LBM_BATCH_PERSISTENT, tx, bps});
+    }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;

@@ -16,7 +16,21 @@ struct StepScalars {
   int periodic;         // 1: y wraps (test mode), 0: thermal walls
   CollideConst cc;
   double rho0;          // FP32 shifted storage: g_i = f_i - w_i rho0
-  float f_omega, f_om1, f_cgx, f_cgy;  // float copies of cc for the FP32 collision
+  // Float copies of cc for the FP32 collision.  Their rounding must not bias the
+  // collision: a relative bias e of the equilibrium's momentum multiplies the momentum by
+  // (1 + omega e) every step, which compounds over a run.  So f_om1 = 1 - f_omega exactly
+  // (for 1/2 <= omega <= 2), and the velocity is scaled by c2_iso = 1 / sum_s w_s M_s with
+  // the float32 shell weights w_s the collision uses (M_s = sum of vx^2 over shell s;
+  // exactly c^2 with exact weights), instead of c^2.  (The gravity shift's rounding only
+  // adds a bias of the forcing, about 6e-8 of it, which does not compound.)
+  float f_omega, f_om1, f_cgx, f_cgy;
+  double c2_iso;
+  // FP32_CONSERVED: gravity over c (gx / c, gy / c) and |g|^2 / c^2 (with the momentum,
+  // the energy the collision adds, in integer-velocity units), and the mass and energy
+  // correction's basis over all 37 populations with the float32 weights: 1 / sum w,
+  // m = sum w |v|^2 / sum w and 1 / sum w (|v|^2 - m)^2
+  double corr_gx, corr_gy, corr_g2, corr_iw, corr_m, corr_ivar;
+  int conserve;  // 1 for LBM_FP32_CONSERVED
   // FP32 moment sums: of g_i 2^(52-k), 2^k <= rho0 < 2^(k+1) (k >= 0), valid for
   // |g_i| < f_fix_range = 8 * 2^k; split constants 48 * 2^k, 1.5 * 2^(k-18), 2^(52-k)
   // (step_fp32.cuh); fix_back = 2^(k-52) turns the sums into moments

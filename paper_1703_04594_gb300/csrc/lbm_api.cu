@@ -27,7 +27,8 @@ bool d2q37::params_valid(const lbm_params* p) {
   if (!p) return false;
   if (p->lx < 4 || p->ly < 6) return false;
   if (!(p->tau > 0.5) || !(p->tau < 1e6)) return false;
-  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED && p->precision != LBM_FP64_FIXED)
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED && p->precision != LBM_FP64_FIXED &&
+      p->precision != LBM_FP32_CONSERVED)
     return false;
   if (p->bc != LBM_BC_WALLS && p->bc != LBM_BC_PERIODIC_Y) return false;
   // grid.y = ceil(lx / 4) must fit in 65535; 37 * lx * pitch must fit the index math
@@ -48,7 +49,10 @@ namespace {
 bool params_ok(const lbm_params* p) { return params_valid(p); }
 
 int64_t pitch_of(const lbm_params* p) { return ((int64_t)p->ly + 31) / 32 * 32; }
-int64_t elem_size(const lbm_params* p) { return p->precision == LBM_FP32_SHIFTED ? 4 : 8; }
+bool fp32_storage(const lbm_params* p) {
+  return p->precision == LBM_FP32_SHIFTED || p->precision == LBM_FP32_CONSERVED;
+}
+int64_t elem_size(const lbm_params* p) { return fp32_storage(p) ? 4 : 8; }
 int64_t state_bytes(const lbm_params* p) { return (int64_t)Q * p->lx * pitch_of(p) * elem_size(p); }
 
 bool aligned16(const void* ptr) { return ptr && ((uintptr_t)ptr % 16) == 0; }
@@ -84,9 +88,31 @@ StepArgs d2q37::make_step_args(const lbm_params* p) {
   a.cc.tshift = tau * (1.0 - tau) * (p->gx * p->gx + p->gy * p->gy) / D - 1.0;
   a.rho0 = p->rho0;
   a.f_omega = (float)a.cc.omega;
-  a.f_om1 = (float)a.cc.om1;
+  a.f_om1 = 1.0f - a.f_omega;  // exact for 1/2 <= omega <= 2
   a.f_cgx = (float)a.cc.cgx;
   a.f_cgy = (float)a.cc.cgy;
+  {
+    double s = 0.0;  // sum_s w_s M_s with the float32 weights of the FP32 collision
+    for (int i = 0; i < Q; ++i) s += (double)(float)weight(i) * (double)(vx(i) * vx(i));
+    a.c2_iso = 1.0 / s;
+    // the mass and energy correction's basis: all 37 populations, float32 weights
+    double sw = 0.0, swq = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      const double w = (double)(float)weight(i);
+      sw += w;
+      swq += w * v2(i);
+    }
+    const double m = swq / sw;
+    double var = 0.0;
+    for (int i = 0; i < Q; ++i) var += (double)(float)weight(i) * (v2(i) - m) * (v2(i) - m);
+    a.corr_iw = 1.0 / sw;
+    a.corr_m = m;
+    a.corr_ivar = 1.0 / var;
+  }
+  a.corr_gx = p->gx / C;
+  a.corr_gy = p->gy / C;
+  a.corr_g2 = (p->gx * p->gx + p->gy * p->gy) / C2;
+  a.conserve = p->precision == LBM_FP32_CONSERVED;
   int k = 0;  // 2^k <= rho0 < 2^(k+1), k >= 0
   while (k < 100 && p->rho0 >= std::ldexp(1.0, k + 1)) ++k;
   a.f_split_c1 = (float)std::ldexp(48.0, k);
@@ -109,7 +135,8 @@ StepArgs d2q37::make_step_args(const lbm_params* p) {
 }
 
 cudaError_t d2q37::launch_step(const void* fin, void* fout, const StepArgs& a, int32_t precision, cudaStream_t s) {
-  if (precision == LBM_FP32_SHIFTED) return launch_step_fp32((const float*)fin, (float*)fout, a, s);
+  if (precision == LBM_FP32_SHIFTED || precision == LBM_FP32_CONSERVED)
+    return launch_step_fp32((const float*)fin, (float*)fout, a, s);
   if (precision == LBM_FP64_FIXED) return launch_step_fix64((const double*)fin, (double*)fout, a, s);
   return launch_step_fp64((const double*)fin, (double*)fout, a, s);
 }
@@ -145,7 +172,7 @@ int32_t lbm_init(const lbm_params* p, const double* rho, const double* ux, const
   if (!params_ok(p) || !aligned8(rho) || !aligned8(ux) || !aligned8(uy) || !aligned8(T) || !aligned16(f))
     return LBM_EINVAL;
   const StepArgs a = make_args(p);
-  if (p->precision == LBM_FP32_SHIFTED)
+  if (fp32_storage(p))
     return cuda_status(launch_init_fp32(rho, ux, uy, T, (float*)f, a, as_stream(stream)));
   return cuda_status(launch_init_fp64(rho, ux, uy, T, (double*)f, a, as_stream(stream)));
 }
@@ -203,7 +230,7 @@ int32_t lbm_moments(const lbm_params* p, const void* f, double* rho, double* ux,
   if (!params_ok(p) || !aligned16(f) || !aligned8(rho) || !aligned8(ux) || !aligned8(uy) || !aligned8(T))
     return LBM_EINVAL;
   const StepArgs a = make_args(p);
-  if (p->precision == LBM_FP32_SHIFTED)
+  if (fp32_storage(p))
     return cuda_status(launch_moments_fp32((const float*)f, rho, ux, uy, T, a, as_stream(stream)));
   return cuda_status(launch_moments_fp64((const double*)f, rho, ux, uy, T, a, as_stream(stream)));
 }
@@ -218,7 +245,7 @@ int32_t lbm_kinetic_energy(const lbm_params* p, const void* f, double* out, void
   if (!params_ok(p) || !aligned16(f) || !aligned8(out) || !aligned8(scratch)) return LBM_EINVAL;
   const StepArgs a = make_args(p);
   if ((int64_t)scratch_bytes < ke_partial_count(a) * (int64_t)sizeof(double)) return LBM_EINVAL;
-  if (p->precision == LBM_FP32_SHIFTED)
+  if (fp32_storage(p))
     return cuda_status(launch_kinetic_energy_fp32((const float*)f, out, (double*)scratch, a, as_stream(stream)));
   return cuda_status(launch_kinetic_energy_fp64((const double*)f, out, (double*)scratch, a, as_stream(stream)));
 }

@@ -58,6 +58,47 @@ __device__ __forceinline__ Fix3 split3(float v, const SplitConst& k) {
   return {__float_as_int(h1) - k.b1, __float_as_int(h2) - k.b2, __float_as_int(h3) - __float_as_int(C3)};
 }
 
+// The first two parts of split3: v * 2^(41-k) ~ H * 2^23 + R, dropping the rest r2
+// (|r2| <= 2^(k-42)).  Enough for sums that only need an absolute error far below float32
+// rounding (37 values: below 2^(k-36)).
+struct Fix2 {
+  int H, R;
+};
+
+__device__ __forceinline__ Fix2 split2(float v, const SplitConst& k) {
+  const float h1 = __fadd_rn(v, k.c1);
+  const float r1 = __fsub_rn(v, __fsub_rn(h1, k.c1));
+  const float h2 = __fadd_rn(r1, k.c2);
+  return {__float_as_int(h1) - k.b1, __float_as_int(h2) - k.b2};
+}
+
+// Running sums of the collision's outputs (mass, sum |v|^2 f, sum vx f, sum vy f) in the
+// two lanes of split2.
+struct OutSums {
+  int rH = 0, rR = 0, eH = 0, eR = 0, xH = 0, xR = 0, yH = 0, yR = 0;
+  // one opposite pair (v, -v): the sum and difference of the two values' lanes
+  __device__ __forceinline__ void add_pair(float a, float b, int vx, int vy, const SplitConst& k) {
+    const Fix2 za = split2(a, k), zb = split2(b, k);
+    const int PH = za.H + zb.H, PR = za.R + zb.R, MH = za.H - zb.H, MR = za.R - zb.R;
+    const int q = vx * vx + vy * vy;
+    rH += PH;
+    rR += PR;
+    eH += q * PH;
+    eR += q * PR;
+    xH += vx * MH;
+    xR += vx * MR;
+    yH += vy * MH;
+    yR += vy * MR;
+  }
+  __device__ __forceinline__ void add_rest(float a, const SplitConst& k) {
+    const Fix2 z = split2(a, k);
+    rH += z.H;
+    rR += z.R;
+  }
+};
+
+__device__ __forceinline__ long long join2(int H, int R) { return ((long long)H << 23) + (long long)R; }
+
 // Moments of the stored deviations: sum g, sum vx g, sum vy g, sum |v|^2 g.  The step
 // uses the momentum in float32 (JT = float), the moments kernels in float64.
 template <class JT>
@@ -81,14 +122,19 @@ __device__ __forceinline__ long long join3(int H, int R, int L) {
 // SCALED = false is the common case k = 0 (rho0 < 2), with every constant an immediate;
 // SCALED = true reads the lattice's constants (a separate instantiation, so the common
 // one keeps its registers).
-template <class JT, bool SCALED>
-__device__ __forceinline__ DevMoments<JT> moments_fix(const float (&g)[Q], const StepScalars& a) {
+// The four exact sums of v_i 2^(52-k) over the 37 values (the lattice's split constants):
+// sum, sum |v|^2, sum vx, sum vy.
+struct FixSums {
+  long long R, E, X, Y;
+};
+
+template <bool SCALED>
+__device__ __forceinline__ SplitConst split_const(const StepScalars& a) {
   constexpr SplitConst s0 = {48.0f, 5.7220458984375e-06f, 4503599627370496.0f, 0x42400000, 0x36c00000};
-  const SplitConst s = SCALED ? SplitConst{a.f_split_c1, a.f_split_c2, a.f_split_s, a.i_split_b1, a.i_split_b2} : s0;
-  const float range = SCALED ? a.f_fix_range : 8.0f;
-  bool in_range = true;  // every |g_i| < 8 * 2^k (false for an infinity or NaN)
-#pragma unroll
-  for (int i = 0; i < Q; ++i) in_range &= fabsf(g[i]) < range;
+  return SCALED ? SplitConst{a.f_split_c1, a.f_split_c2, a.f_split_s, a.i_split_b1, a.i_split_b2} : s0;
+}
+
+__device__ __forceinline__ FixSums fix_sums(const float (&g)[Q], const SplitConst& s) {
   const Fix3 z = split3(g[0], s);
   int rH = z.H, rR = z.R, rL = z.L;
   int eH = 0, eR = 0, eL = 0, xH = 0, xR = 0, xL = 0, yH = 0, yR = 0, yL = 0;
@@ -114,22 +160,64 @@ __device__ __forceinline__ DevMoments<JT> moments_fix(const float (&g)[Q], const
       yL += rep_vy(k) * ML;
     }
   }
-  // back from the sums of g 2^(52-k): times 2^(k-52)
-  const double back = SCALED ? a.fix_back : 1.0 / 4503599627370496.0;
+  return {join3(rH, rR, rL), join3(eH, eR, eL), join3(xH, xR, xL), join3(yH, yR, yL)};
+}
+
+// Every |g_i| < 8 * 2^k (false for an infinity or NaN): the storage range of the form.
+template <bool SCALED>
+__device__ __forceinline__ bool fix_in_range(const float (&g)[Q], const StepScalars& a) {
+  const float range = SCALED ? a.f_fix_range : 8.0f;
+  bool in_range = true;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) in_range &= fabsf(g[i]) < range;
+  return in_range;
+}
+
+// 2^(k-52): from the fixed-point sums back to moments.
+template <bool SCALED>
+__device__ __forceinline__ double fix_back(const StepScalars& a) {
+  return SCALED ? a.fix_back : 1.0 / 4503599627370496.0;
+}
+
+template <class JT, bool SCALED>
+__device__ __forceinline__ DevMoments<JT> moments_of(const FixSums& f, bool in_range, const StepScalars& a) {
+  const double back = fix_back<SCALED>(a);
   const JT back_j = SCALED ? (JT)(sizeof(JT) == 4 ? a.f_fix_back : a.fix_back) : (JT)(1.0 / 4503599627370496.0);
   DevMoments<JT> r;
-  r.drho = (double)join3(rH, rR, rL) * back;
-  r.de = (double)join3(eH, eR, eL) * back;
-  r.jx = (JT)join3(xH, xR, xL) * back_j;
-  r.jy = (JT)join3(yH, yR, yL) * back_j;
+  r.drho = (double)f.R * back;
+  r.de = (double)f.E * back;
+  r.jx = (JT)f.X * back_j;
+  r.jy = (JT)f.Y * back_j;
   if (!in_range) r.drho = __longlong_as_double(0x7FF8000000000000LL);  // rho, and so every output, NaN
   return r;
 }
 
+template <class JT, bool SCALED>
+__device__ __forceinline__ DevMoments<JT> moments_fix(const float (&g)[Q], const StepScalars& a) {
+  return moments_of<JT, SCALED>(fix_sums(g, split_const<SCALED>(a)), fix_in_range<SCALED>(g, a), a);
+}
+
 // Collision of one site in the precision split described at the top of the file.
-template <bool SCALED, class Store>
-__device__ __forceinline__ void collide_site_fp32(const float (&g)[Q], const StepScalars& a, Store&& store) {
-  const DevMoments<float> m = moments_fix<float, SCALED>(g, a);
+//
+// CONSERVE: restore the exact post-collision mass, momentum and energy after the float32
+// arithmetic.  Float32 rounding in the equilibrium changes a site's mass, momentum and
+// energy by a few units of 2^-24 of the deviations; conserved quantities are never relaxed
+// away, so that noise accumulates and dominates the velocity error of long runs (mass and
+// energy as pressure noise early on, momentum more and more as the flow develops).  The
+// collision's exact post-collision values are known in closed form (eq. "lbequation" with
+// the shifted equilibrium, omega tau = 1): mass unchanged, momentum J + rho g, energy
+// E + rho (2 u.g + |g|^2).  The outputs are summed as they are formed (split2: absolute
+// error below 2^-36, against rounding noise of ~1e-8), and the difference is put back along
+// the first Hermite polynomials over all 37 populations,
+// delta_i = w_i [alpha + beta . v_i + gamma (|v_i|^2 - m)], m = sum w |v|^2 / sum w: the
+// shape of the equilibrium's own density, velocity and temperature response, which disturbs
+// the other moments least.
+template <bool SCALED, bool CONSERVE, class Store>
+__device__ __forceinline__ void collide_site_fp32(float (&g)[Q], const StepScalars& a, Store&& store) {
+  const SplitConst sc = split_const<SCALED>(a);
+  const bool in_range = fix_in_range<SCALED>(g, a);
+  const FixSums in = fix_sums(g, sc);
+  const DevMoments<float> m = moments_of<float, SCALED>(in, in_range, a);
   // float64: density, energy, temperature
   const double drho = m.drho;
   const double rho = a.rho0 + drho;
@@ -139,7 +227,9 @@ __device__ __forceinline__ void collide_site_fp32(const float (&g)[Q], const Ste
   const double r0 = (double)r_f;
   const double inv = fma(r0, fma(-rho, r0, 1.0), r0);
   // float32: velocity c u = c^2 j / rho
-  const float c2ir_f = (float)C2 * r_f;
+  // c u = c^2 j / rho with the velocity scale c2_iso in place of c^2 (see StepScalars):
+  // with it the float32 equilibrium's first-order momentum is exactly rho u
+  const float c2ir_f = (float)(a.c2_iso * inv);
   const float Ux0 = (float)m.jx * c2ir_f, Uy0 = (float)m.jy * c2ir_f;
   const float uu = fmaf(Ux0, Ux0, Uy0 * Uy0) * (float)(1.0 / C2);
   // t = T_s - 1 = (c^2 e / rho - |u|^2) / D + tau (1 - tau) |g|^2 / D - 1: the large part in
@@ -175,7 +265,14 @@ __device__ __forceinline__ void collide_site_fp32(const float (&g)[Q], const Ste
   float X[4] = {0.0f, Ux, Ux + Ux, 0.0f}, Y[4] = {0.0f, Uy, Uy + Uy, 0.0f};
   X[3] = X[2] + Ux;
   Y[3] = Y[2] + Uy;
-  store(0, fmaf(om1, g[0], K0[0]));
+  OutSums os;
+  // CONSERVE holds the outputs in g (each g_i is dead once its output is formed)
+  const auto out = [&](int i, float v) {
+    if (CONSERVE) g[i] = v;
+    else store(i, v);
+  };
+  out(0, fmaf(om1, g[0], K0[0]));
+  if (CONSERVE) os.add_rest(g[0], sc);
 #pragma unroll
   for (int j = 1; j <= NPAIR; ++j) {
     const int sh = shell(j), vxk = rep_vx(j), vyk = rep_vy(j);
@@ -186,8 +283,34 @@ __device__ __forceinline__ void collide_site_fp32(const float (&g)[Q], const Ste
     const float s2 = s * s;
     const float E = fmaf(fmaf(K4[sh], s2, K2[sh]), s2, K0[sh]);
     const float O = s * fmaf(K3[sh], s2, K1[sh]);
-    store(j, fmaf(om1, g[j], E + O));
-    store(j + NPAIR, fmaf(om1, g[j + NPAIR], E - O));
+    out(j, fmaf(om1, g[j], E + O));
+    out(j + NPAIR, fmaf(om1, g[j + NPAIR], E - O));
+    if (CONSERVE) os.add_pair(g[j], g[j + NPAIR], vxk, vyk, sc);
+  }
+  if constexpr (CONSERVE) {
+    // split2 sums are in units of 2^(k-41), the exact input sums in units of 2^(k-52)
+    const double back = fix_back<SCALED>(a), back2 = back * 2048.0;
+    const double jx = (double)in.X * back, jy = (double)in.Y * back;
+    // what the outputs lack: exact input sums minus output sums, plus the forcing
+    const double dM = (double)in.R * back - (double)join2(os.rH, os.rR) * back2;
+    const double dJx = fma(rho, a.corr_gx, (double)in.X * back - (double)join2(os.xH, os.xR) * back2);
+    const double dJy = fma(rho, a.corr_gy, (double)in.Y * back - (double)join2(os.yH, os.yR) * back2);
+    const double dE = fma(rho, a.corr_g2, fma(2.0 * jx, a.corr_gx, fma(2.0 * jy, a.corr_gy,
+                                                                      (double)in.E * back - (double)join2(os.eH, os.eR) * back2)));
+    const float alpha = (float)(dM * a.corr_iw);
+    const float gamma = (float)(fma(-dM, a.corr_m, dE) * a.corr_ivar);
+    // sum_i w_i vx_i^2 = 1 / c2_iso for the float32 weights (see StepScalars)
+    const float bx = (float)(a.c2_iso * dJx), by = (float)(a.c2_iso * dJy);
+    const float mf = (float)a.corr_m;
+    store(0, g[0] + (float)w_shell(0) * fmaf(gamma, -mf, alpha));
+#pragma unroll
+    for (int j = 1; j <= NPAIR; ++j) {
+      const float ws = (float)w_shell(shell(j));
+      const float A = ws * fmaf(gamma, (float)v2(j) - mf, alpha);
+      const float B = fmaf(ws * (float)rep_vx(j), bx, (ws * (float)rep_vy(j)) * by);
+      store(j, g[j] + (A + B));
+      store(j + NPAIR, g[j + NPAIR] + (A - B));
+    }
   }
 }
 
@@ -215,8 +338,9 @@ __device__ __forceinline__ void wall_drho(const float* __restrict__ fin, int x, 
 
 
 // One warp-strip of the FP32 shifted step (see step_fp64.cuh for the strip contract).
-// SCALED: the lattice's reference density is 2 or more (see moments_fix).
-template <bool PERIODIC, bool SCALED, class Ld>
+// SCALED: the lattice's reference density is 2 or more (see moments_fix); CONSERVE: the
+// collision restores the exact conserved moments (collide_site_fp32).
+template <bool PERIODIC, bool SCALED, bool CONSERVE, class Ld>
 __device__ __forceinline__ void step_strip_fp32(const float* __restrict__ fin, float* __restrict__ fout,
                                                 const StepScalars& a, const StepWalls& w, int x, int y0, Ld ld) {
   const int y = y0 + (threadIdx.x & 31);
@@ -252,7 +376,7 @@ __device__ __forceinline__ void step_strip_fp32(const float* __restrict__ fin, f
   }
   if (!active) return;
   const unsigned self = (unsigned)((long long)x * a.pitch + y);
-  collide_site_fp32<SCALED>(g, a, [&](int i, float v) { __stcs(fout + i * a.pop + self, v); });
+  collide_site_fp32<SCALED, CONSERVE>(g, a, [&](int i, float v) { __stcs(fout + i * a.pop + self, v); });
 }
 
 }  // namespace d2q37

@@ -16,7 +16,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_native", "liblbm_d2q37.so")
 
-FP64, FP32_SHIFTED, FP64_FIXED = 0, 1, 2
+FP64, FP32_SHIFTED, FP64_FIXED, FP32_CONSERVED = 0, 1, 2, 3
 BC_WALLS, BC_PERIODIC_Y = 0, 1
 Q = 37
 
@@ -170,7 +170,7 @@ def buffer_bytes(p: Params) -> int:
 
 
 def state_dtype(p: Params):
-    return torch.float32 if p.precision == FP32_SHIFTED else torch.float64
+    return torch.float32 if p.precision in (FP32_SHIFTED, FP32_CONSERVED) else torch.float64
 
 
 def empty_state(p: Params, device="cuda") -> torch.Tensor:

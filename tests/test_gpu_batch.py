@@ -64,7 +64,7 @@ def assert_equal_states(params, got, want):
         assert torch.equal(g[:, :, : p.ly], w[:, :, : p.ly]), p
 
 
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_SHIFTED, lbm.FP64_FIXED])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32_SHIFTED, lbm.FP64_FIXED, lbm.FP32_CONSERVED])
 @pytest.mark.parametrize("mode,tx", [(lbm.BATCH_PER_STEP, 4), (lbm.BATCH_PER_STEP, 1), (lbm.BATCH_PER_STEP, 8),
                                       (lbm.BATCH_PERSISTENT, 4), (lbm.BATCH_PERSISTENT, 2), (lbm.BATCH_LOOP, 4)])
 def test_batch_equals_single_lattice_runs(precision, mode, tx):
@@ -84,7 +84,7 @@ def test_batch_equals_single_lattice_runs(precision, mode, tx):
 ORACLE_STEPS = 5
 
 
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP64_FIXED, lbm.FP32_SHIFTED])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP64_FIXED, lbm.FP32_SHIFTED, lbm.FP32_CONSERVED])
 @pytest.mark.parametrize("mode", [lbm.BATCH_PER_STEP, lbm.BATCH_PERSISTENT])
 @pytest.mark.parametrize("bc", [lbm.BC_WALLS, lbm.BC_PERIODIC_Y])
 def test_batch_matches_oracle(precision, mode, bc):
@@ -101,7 +101,7 @@ def test_batch_matches_oracle(precision, mode, bc):
     assert b.status() == lbm.OK
     for p, got, fl in zip(params, b.states(), fields):
         want = OL.run(OL.init_equilibrium(*fl), oracle_params(p), ORACLE_STEPS)
-        if precision == lbm.FP32_SHIFTED:
+        if precision in (lbm.FP32_SHIFTED, lbm.FP32_CONSERVED):
             err = field_errors([t.cpu() for t in lbm.moments(p, got)], OL.fields(want))
             assert max(err[k] for k in ("rho_max", "rho_rms", "T_max", "T_rms", "u_max_cs")) <= 1e-5, (p, err)
         else:

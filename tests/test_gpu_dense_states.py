@@ -8,9 +8,9 @@ sum_i |v_i|^2 f_i reach 2233 and 6980, beyond 2^11), and a density ramp that cro
 bound inside one warp, through every float64 entry point, and hold them to the same bars as
 the ordinary states: populations within 1e-12 relative of the oracle after 3 steps.
 
-The FP32 shifted form stores g_i = f_i - w_i rho0 and states its own range, |g_i| < 8:
-with rho0 at the state's density it meets its per-field bar; with rho0 = 1 every site is
-outside the range and comes out NaN.
+The FP32 forms store g_i = f_i - w_i rho0 and state their own range, |g_i| < 8 * 2^k with
+2^k <= rho0 < 2^(k+1): with rho0 at the state's density they meet their per-field bar;
+with rho0 = 1 every site of a density-1600 state is outside the range and comes out NaN.
 """
 import pytest
 import torch
@@ -169,14 +169,15 @@ def test_adjoint_step_matches_oracle_vjp(kind, bc):
     assert abs(float(dtau) - float(tau_t.grad)) <= 1e-10 * abs(float(tau_t.grad))
 
 
-def fp32(p, rho0):
+def fp32(p, rho0, precision=lbm.FP32_SHIFTED):
     return lbm.Params(p.lx, p.ly, tau=p.tau, gx=p.gx, gy=p.gy, t_bottom=p.t_bottom, t_top=p.t_top,
-                      rho0=rho0, precision=lbm.FP32_SHIFTED, bc=p.bc)
+                      rho0=rho0, precision=precision, bc=p.bc)
 
 
+@pytest.mark.parametrize("precision", [lbm.FP32_SHIFTED, lbm.FP32_CONSERVED])
 @pytest.mark.parametrize("kind,rho0", [("rt1600", 1600.0), ("rest1600", 1600.0), ("rt5000", 5000.0)])
-def test_fp32_with_matching_reference_density(kind, rho0):
-    p = fp32(params(lbm.BC_WALLS), rho0)
+def test_fp32_with_matching_reference_density(kind, rho0, precision):
+    p = fp32(params(lbm.BC_WALLS), rho0, precision)
     fields = dense_fields(p, kind)
     f = device_init(p, fields)
     res = lbm.run(p, f, lbm.empty_state(p), STEPS)
