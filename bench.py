@@ -53,10 +53,28 @@ BYTES_PER_SITE_FP64 = 592          # 37 x 8 B read + 37 x 8 B written
 BYTES_PER_SITE_FP32 = 296          # 37 x 4 B read + 37 x 4 B written
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture
-# of the current kernel on a smaller lattice, scaled to the bench's lattice by the site
-# count; profiles/ holds the captures).  None where no capture of the current kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = {"fused": None, "separate": None, "fp32": None, "fp64fix": None, "adjoint": None}
+# DRAM bytes per site (dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
+# current kernel, from an ncu capture on a smaller lattice or batch, divided by its sites;
+# profiles/ holds the captures).  A launch's `traffic` is this times its sites.  None where
+# no capture of the current kernel exists.  Reads equal the algorithmic bytes; writes read
+# a little low on the captured cases because their tail is still in L2 when the kernel ends.
+TRAFFIC_BYTES_PER_SITE = {
+    "fused": 540.5,        # k_step_fp64, 512 x 2048
+    "fp64fix": 569.2,      # k_step_fix64, 1024 x 2048
+    "fp32": 272.8,         # k_step_fp32 (shifted), 1024 x 2048
+    "fp32c": None,         # k_step_fp32 (conserved moments): changed since its capture
+    "adjoint": 851.4,      # k_adj_collide, 512 x 1024 (the adjoint workload's own lattice)
+    "batch_fp32": 259.4,   # k_batch_step<fp32>, 64 small lattices
+    "batch_fp64": 587.2,   # k_batch_step<double>, 8 lattices Lx 128..1024
+    "separate": None,
+}
+
+
+def traffic(key, sites):
+    """DRAM bytes of one launch over `sites` sites, from the captured bytes per site."""
+    b = TRAFFIC_BYTES_PER_SITE.get(key)
+    return None if b is None else b * sites
+
 
 
 def _hbm_peak(root=None):
@@ -296,13 +314,13 @@ def run_ours(a):
     if fp32 or fix:
         achieved = (BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64) * sites / (kern_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": achieved / HBM_PEAK_GBS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(a.precision),
+                    "frac": achieved / HBM_PEAK_GBS, "traffic": traffic(a.precision, sites),
                     "kernel": "k_step_fp32" if fp32 else "k_step_fix64",
                     "peak_source": HBM_PEAK_SOURCE}
     else:
         achieved = FLOPS_PER_SITE_FP64 * sites / (kern_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(a.variant),
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic(a.variant, sites),
                     "peak_measured": fp64_measured,
                     "frac_of_measured": achieved / fp64_measured if fp64_measured else None,
                     "kernel": {"fused": "k_step_fp64", "separate": "whole step (3 kernels)",
@@ -357,7 +375,7 @@ def run_ours(a):
                               "integer pipes (float64 outside its range); same parity bars as FP64",
                       "roofline": {"bound": "hbm", "achieved": f_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                                    "frac": f_gbs / HBM_PEAK_GBS,
-                                   "traffic": TRAFFIC_BYTES_PER_LAUNCH.get("fp64fix"),
+                                   "traffic": traffic("fp64fix", sites),
                                    "peak_source": HBM_PEAK_SOURCE},
                       "gpu_launches": a.steps, "clocks": fclk.summary()}
 
@@ -474,7 +492,7 @@ def single_form(a, precision, dev_fields):
            "dtype": "f32+i64+f64" if fp32 else "f64+i64",
            "workload": f"{LX}x{LY} RT lattice, seed {SEED}",
            "roofline": kernel_roofline("hbm", BYTES_PER_SITE_FP32 if fp32 else BYTES_PER_SITE_FP64, sites, ms,
-                                       kernel, TRAFFIC_BYTES_PER_LAUNCH.get(precision)),
+                                       kernel, traffic(precision, sites)),
            "gpu_launches": a.steps, "clocks": clk.summary()}
     del bufs
     torch.cuda.empty_cache()
@@ -564,10 +582,13 @@ def batch_roofline(precision, sites, ms_step, cfg):
 
     kname = {"fp32": "fp32", "fp32c": "fp32 conserved", "fp64fix": "fix64", "fp64": "double"}[precision]
     kernel = ("k_batch_persistent<" if cfg["mode"] == lbm.BATCH_PERSISTENT else "k_batch_step<") + kname + ">"
+    # the captures are of the per-step kernel
+    tr = (traffic({"fp32": "batch_fp32", "fp64": "batch_fp64"}.get(precision, ""), sites)
+          if cfg["mode"] == lbm.BATCH_PER_STEP else None)
     if precision == "fp64":
-        return kernel_roofline("alu", FLOPS_PER_SITE_FP64, sites, ms_step, kernel)
+        return kernel_roofline("alu", FLOPS_PER_SITE_FP64, sites, ms_step, kernel, tr)
     return kernel_roofline("hbm", BYTES_PER_SITE_FP32 if precision in ("fp32", "fp32c") else BYTES_PER_SITE_FP64, sites,
-                           ms_step, kernel)
+                           ms_step, kernel, tr)
 
 
 def batch_form(a, precision, kind="uneven", n=None, seed=4):
@@ -697,7 +718,7 @@ def run_adjoint_step(a):
                       "config": {"workload": f"lbm_adjoint_step on a {lx}x{ly} RT state"},
                       "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms,
                                                   "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
-                                                  TRAFFIC_BYTES_PER_LAUNCH.get("adjoint")),
+                                                  traffic("adjoint", sites)),
                       "clocks": clk}), flush=True)
 
 
@@ -759,7 +780,7 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
             "adjoint_step_ms": ms_adj,
             "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms_adj,
                                         "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
-                                        TRAFFIC_BYTES_PER_LAUNCH.get("adjoint")),
+                                        traffic("adjoint", sites)),
             "clocks": clk.summary(), "adjoint_step_clocks": aclk}
 
 

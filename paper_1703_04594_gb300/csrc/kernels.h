@@ -30,6 +30,9 @@ struct StepScalars {
   // correction's basis over all 37 populations with the float32 weights: 1 / sum w,
   // m = sum w |v|^2 / sum w and 1 / sum w (|v|^2 - m)^2
   double corr_gx, corr_gy, corr_g2, corr_iw, corr_m, corr_ivar;
+  // float copies for the correction's float32 arithmetic (gravity over c as hi + lo pairs)
+  float f_corr_gx_hi, f_corr_gx_lo, f_corr_gy_hi, f_corr_gy_lo, f_corr_g2, f_corr_iw, f_corr_m, f_corr_ivar,
+      f_c2_iso;
   int conserve;  // 1 for LBM_FP32_CONSERVED
   // FP32 moment sums: of g_i 2^(52-k), 2^k <= rho0 < 2^(k+1) (k >= 0), valid for
   // |g_i| < f_fix_range = 8 * 2^k; split constants 48 * 2^k, 1.5 * 2^(k-18), 2^(52-k)

@@ -12,10 +12,9 @@ namespace d2q37 {
 #define LBM_FP32_MIN_BLOCKS 6  // 80 registers; measured best among 4..8 blocks per SM
 #endif
 // The conserved-moment form holds all 37 outputs and eight sum lanes until its
-// correction.  At 6 blocks per SM (80 registers) it spills 48 bytes and still measured
-// faster than at 5 (96 registers, no spill): 11.1 k against 11.0 k MLUPS on 4096 x 8192.
+// correction: 5 blocks per SM (96 registers) instead of spilling at 80.
 #ifndef LBM_FP32C_MIN_BLOCKS
-#define LBM_FP32C_MIN_BLOCKS 6
+#define LBM_FP32C_MIN_BLOCKS 5
 #endif
 template <bool PERIODIC, bool SCALED, bool CONSERVE>
 __global__ void __launch_bounds__(128, CONSERVE ? LBM_FP32C_MIN_BLOCKS : LBM_FP32_MIN_BLOCKS) k_step_fp32(

@@ -113,6 +113,15 @@ StepArgs d2q37::make_step_args(const lbm_params* p) {
   a.corr_gy = p->gy / C;
   a.corr_g2 = (p->gx * p->gx + p->gy * p->gy) / C2;
   a.conserve = p->precision == LBM_FP32_CONSERVED;
+  a.f_corr_gx_hi = (float)a.corr_gx;
+  a.f_corr_gx_lo = (float)(a.corr_gx - (double)a.f_corr_gx_hi);
+  a.f_corr_gy_hi = (float)a.corr_gy;
+  a.f_corr_gy_lo = (float)(a.corr_gy - (double)a.f_corr_gy_hi);
+  a.f_corr_g2 = (float)a.corr_g2;
+  a.f_corr_iw = (float)a.corr_iw;
+  a.f_corr_m = (float)a.corr_m;
+  a.f_corr_ivar = (float)a.corr_ivar;
+  a.f_c2_iso = (float)a.c2_iso;
   int k = 0;  // 2^k <= rho0 < 2^(k+1), k >= 0
   while (k < 100 && p->rho0 >= std::ldexp(1.0, k + 1)) ++k;
   a.f_split_c1 = (float)std::ldexp(48.0, k);

@@ -288,20 +288,24 @@ __device__ __forceinline__ void collide_site_fp32(float (&g)[Q], const StepScala
     if (CONSERVE) os.add_pair(g[j], g[j + NPAIR], vxk, vyk, sc);
   }
   if constexpr (CONSERVE) {
-    // split2 sums are in units of 2^(k-41), the exact input sums in units of 2^(k-52)
-    const double back = fix_back<SCALED>(a), back2 = back * 2048.0;
-    const double jx = (double)in.X * back, jy = (double)in.Y * back;
-    // what the outputs lack: exact input sums minus output sums, plus the forcing
-    const double dM = (double)in.R * back - (double)join2(os.rH, os.rR) * back2;
-    const double dJx = fma(rho, a.corr_gx, (double)in.X * back - (double)join2(os.xH, os.xR) * back2);
-    const double dJy = fma(rho, a.corr_gy, (double)in.Y * back - (double)join2(os.yH, os.yR) * back2);
-    const double dE = fma(rho, a.corr_g2, fma(2.0 * jx, a.corr_gx, fma(2.0 * jy, a.corr_gy,
-                                                                      (double)in.E * back - (double)join2(os.eH, os.eR) * back2)));
-    const float alpha = (float)(dM * a.corr_iw);
-    const float gamma = (float)(fma(-dM, a.corr_m, dE) * a.corr_ivar);
+    // What the outputs lack, in integers: the exact input sums (units of 2^(k-52)) minus the
+    // output sums (split2, units of 2^(k-41)); then, in float32 (the differences are ~1e-8),
+    // plus the forcing.  No float64 arithmetic: this form is otherwise bound by that pipe.
+    const float backf = SCALED ? a.f_fix_back : 2.220446049250313e-16f;  // 2^(k-52)
+    const float dM = (float)(in.R - (join2(os.rH, os.rR) << 11)) * backf;
+    const float dX = (float)(in.X - (join2(os.xH, os.xR) << 11)) * backf;
+    const float dY = (float)(in.Y - (join2(os.yH, os.yR) << 11)) * backf;
+    const float dEs = (float)(in.E - (join2(os.eH, os.eR) << 11)) * backf;
+    // momentum: + rho g / c (the constant as a float pair, so the forcing keeps its value);
+    // energy: + 2 j.g / c + rho |g|^2 / c^2
+    const float dJx = fmaf(rho_f, a.f_corr_gx_hi, fmaf(rho_f, a.f_corr_gx_lo, dX));
+    const float dJy = fmaf(rho_f, a.f_corr_gy_hi, fmaf(rho_f, a.f_corr_gy_lo, dY));
+    const float dE = fmaf(rho_f, a.f_corr_g2, fmaf(2.0f * m.jx, a.f_corr_gx_hi, fmaf(2.0f * m.jy, a.f_corr_gy_hi, dEs)));
+    const float alpha = dM * a.f_corr_iw;
+    const float mf = a.f_corr_m;
+    const float gamma = fmaf(-dM, mf, dE) * a.f_corr_ivar;
     // sum_i w_i vx_i^2 = 1 / c2_iso for the float32 weights (see StepScalars)
-    const float bx = (float)(a.c2_iso * dJx), by = (float)(a.c2_iso * dJy);
-    const float mf = (float)a.corr_m;
+    const float bx = a.f_c2_iso * dJx, by = a.f_c2_iso * dJy;
     store(0, g[0] + (float)w_shell(0) * fmaf(gamma, -mf, alpha));
 #pragma unroll
     for (int j = 1; j <= NPAIR; ++j) {
