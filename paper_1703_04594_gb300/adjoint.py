@@ -73,14 +73,20 @@ class _KineticEnergyAfter(torch.autograd.Function):
         side = torch.cuda.Stream(dev) if cuda else None
         if cuda:
             side.wait_stream(main)                         # the checkpoints are ready
+        # two pools of every - 1 recomputed states, used by alternate segments: no allocation
+        # per step, and a segment is recomputed into the pool the adjoint finished with
+        pools = [[lbm.empty_state(p, dev) for _ in range(max(every - 1, 0))] for _ in range(2)]
+        released = [None, None]                            # main-stream events: pool free again
 
-        def recompute(k):
+        def recompute(k, pool):
             """f^k .. f^{end-1} of the segment starting at checkpoint k (on the side stream)."""
             end = min(k + every, n_steps)
             with torch.cuda.stream(side) if cuda else contextlib.nullcontext():
+                if cuda and released[pool] is not None:
+                    side.wait_event(released[pool])
                 states = [ctx.checkpoints[k]]
-                for _ in range(k, end - 1):
-                    nxt = lbm.empty_state(p, dev)
+                for j in range(k, end - 1):
+                    nxt = pools[pool][j - k]
                     lbm.step(p, states[-1], nxt)
                     states.append(nxt)
                 done = None
@@ -89,19 +95,21 @@ class _KineticEnergyAfter(torch.autograd.Function):
                     done.record(side)
             return k, end, states, done
 
-        pending = recompute(order[0])
+        pending = recompute(order[0], 0)
         for idx in range(len(order)):
             k, end, states, done = pending
             if cuda:
                 main.wait_event(done)
-                for t in states:                           # read on the main stream below
-                    t.record_stream(main)
             if idx + 1 < len(order):
-                pending = recompute(order[idx + 1])        # overlaps the adjoint steps below
+                pending = recompute(order[idx + 1], (idx + 1) % 2)   # overlaps the adjoint steps below
             for n in reversed(range(k, end)):
                 lbm.adjoint_step(pa, states[n - k], lam, lam_other, dtau, work)
                 lam, lam_other = lam_other, lam
+            if cuda:
+                released[idx % 2] = torch.cuda.Event()
+                released[idx % 2].record(main)
             del states
+        del pools
         g = lbm.init_adjoint(pa, *ctx.fields, lam)
         g_tau = None
         if ctx.tau_shape is not None:

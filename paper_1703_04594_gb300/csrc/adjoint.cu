@@ -179,8 +179,11 @@ __device__ __forceinline__ void cp_async8_adj(double* smem_dst, const double* gm
 // Step 1: per-site adjoint of the collision with the transposed propagate as its store
 // (block 32 x 4 as the forward kernels).  `side` holds 2 * lx * kGhostSlots doubles: the
 // bottom slots of every column, then the top slots.
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 5  // 96 registers, 20 warps per SM (with 37.9 KB of staging per block)
+#endif
 template <bool PERIODIC>
-__global__ void __launch_bounds__(128, 5) k_adj_collide(const double* __restrict__ fin,
+__global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const double* __restrict__ fin,
                                                      const double* __restrict__ lam_next, double* __restrict__ lam_out,
                                                      double* __restrict__ side, double* __restrict__ dtau_part,
                                                      StepArgs a, double tau, double gx, double gy) {
