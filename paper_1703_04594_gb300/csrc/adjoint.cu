@@ -101,9 +101,8 @@ __device__ __forceinline__ EqVjp eq_vjp_pairs(double rho, double usx, double usy
 
 // The float64 VJP for sites outside the fixed-point range, not inlined so that its
 // unrolled arithmetic does not weigh on the register allocation of the fixed-point path.
-__device__ __noinline__ EqVjp eq_vjp_float64(double rho, double usx, double usy, double t,
-                                             const double* __restrict__ lam, long long pop) {
-  return eq_vjp_pairs(rho, usx, usy, t, [&](int i) { return __ldg(lam + i * pop); });
+__device__ __noinline__ EqVjp eq_vjp_float64(double rho, double usx, double usy, double t, const double* mu_staged) {
+  return eq_vjp_pairs(rho, usx, usy, t, [&](int i) { return mu_staged[i * 32]; });
 }
 
 __device__ __forceinline__ double block_sum_128(double v) {
@@ -224,19 +223,28 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
       const double t = T + tau * (1.0 - tau) * gg / D - 1.0;
       const long long o = (long long)x * a.pitch + y;
       const double* lam = lam_next + o;
-      double mu_ft = 0.0;  // sum_i mu_i f~_i
+      // sum_i mu_i f~_i; each staging slot, once its f~_i is read, takes mu_i = lambda_i, so
+      // the three later passes over mu (the VJP's exponent scan and conversion, the outputs)
+      // read shared memory instead of re-reading lambda, whose 37.9 KB per block do not stay
+      // in the L1 that the staging leaves
+      double mu_ft = 0.0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) mu_ft = fma(__ldg(lam + i * a.pop), fget(i), mu_ft);
+      for (int i = 0; i < Q; ++i) {
+        const double l = __ldg(lam + i * a.pop);
+        mu_ft = fma(l, fget(i), mu_ft);
+        sf[i * 32] = l;
+      }
+      const auto mu = [&](int i) { return sf[i * 32]; };
       // the VJP in fixed point (adjoint_fix64.cuh), in float64 outside its range
       EqVjp G;
       VjpSums V;
-      if (eq_vjp_sums_fix(usx, usy, t, [&](int i) { return __ldg(lam + i * a.pop); }, V)) {
+      if (eq_vjp_sums_fix(usx, usy, t, mu, V)) {
         G.Grho = V.Gr;
         G.Gux = rho * fma(C, V.Ax, 2.0 * usx * V.Wu);
         G.Guy = rho * fma(C, V.Ay, 2.0 * usy * V.Wu);
         G.Gt = rho * V.Gt;
       } else {
-        G = eq_vjp_float64(rho, usx, usy, t, lam, a.pop);
+        G = eq_vjp_float64(rho, usx, usy, t, sf);
       }
       const double nuE = G.Gt * inv / D;
       const double nuJx = G.Gux * inv - 2.0 * ux * G.Gt * inv / D;
@@ -265,13 +273,13 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
       // and B_v = w c nuJ . v (from the multiples of w c nuJ)
       const double wR = om * nuR, wE = om * (C2 * nuE);
       const Multiples wJ = make_multiples(om * (C * nuJx), om * (C * nuJy));
-      push(0, fma(om1, __ldg(lam), wR));
+      push(0, fma(om1, mu(0), wR));
 #pragma unroll
       for (int k = 1; k <= NPAIR; ++k) {
         const double A = fma(wE, (double)v2(k), wR);
         const double B = dot_v(wJ, rep_vx(k), rep_vy(k));
-        push(k, fma(om1, __ldg(lam + k * a.pop), A + B));
-        push(k + NPAIR, fma(om1, __ldg(lam + (k + NPAIR) * a.pop), A - B));
+        push(k, fma(om1, mu(k), A + B));
+        push(k + NPAIR, fma(om1, mu(k + NPAIR), A - B));
       }
       // entries of this site whose source z + v_i lies beyond a wall get no push
       if (!PERIODIC && (y < 3 || y >= a.ly - 3)) {
