@@ -744,28 +744,35 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
         res = lbm.run(p, f, lbm.empty_state(p), n)
         return float(lbm.kinetic_energy(p, res))
 
-    def gradient():
+    def gradient(every=every, recompute=None):
         amp = modes.a.clone().requires_grad_(True)
         tau = torch.tensor(TAU, dtype=torch.float64, requires_grad=True)
         fields = I.rt_fields(lx, ly, I.RTModes(a=amp, phi=modes.phi), T_BOTTOM, T_TOP, abs(GY))
-        e = A.kinetic_energy_after(*[t.cuda() for t in fields], tau, p, n, every)
+        e = A.kinetic_energy_after(*[t.cuda() for t in fields], tau, p, n, every, recompute_precision=recompute)
         e.backward()
         return amp.grad, tau.grad
 
-    forward_only()
-    gradient()
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(repeats):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / repeats
+
     with ClockSampler(0) as clk:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(repeats):
-            forward_only()
-        torch.cuda.synchronize()
-        t_fwd = (time.perf_counter() - t0) / repeats
-        t0 = time.perf_counter()
-        for _ in range(repeats):
-            gradient()
-        torch.cuda.synchronize()
-        t_grad = (time.perf_counter() - t0) / repeats
+        t_fwd = timed(forward_only)
+        t_grad = timed(gradient)
+    # the same gradient under the two other schedules: the segments recomputed with the
+    # fixed-point relaxation, and every state kept in HBM (no recomputation)
+    other = {}
+    if precision != "fp64fix":
+        other["fixed_point_recomputation"] = timed(lambda: gradient(recompute=lbm.FP64_FIXED))
+    other["every_state_kept"] = timed(lambda: gradient(every=1))
+    torch.cuda.empty_cache()
+    schedules = {k: {"gradient_s": v, "gradient_over_forward": v / t_fwd} for k, v in other.items()}
+    schedules["every_state_kept"]["memory_gb"] = (n + 1) * lbm.buffer_bytes(p) / 1e9
     ms_adj, aclk = adjoint_step_ms(lx, ly, modes, warmup=4, calls=40)
     sites = lx * ly
     return {"value": whole_job_mlups(sites, n, 1, t_grad * 1e3), "unit": "MLUPS",
@@ -777,6 +784,7 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
             "gradient_s": t_grad, "forward_s": t_fwd, "gradient_over_forward": t_grad / t_fwd,
             "forward_baseline": {"value": whole_job_mlups(sites, n, 1, t_fwd * 1e3), "unit": "MLUPS",
                                  "what": "the same 500 forward steps and the energy, no gradient"},
+            "other_schedules": schedules,
             "adjoint_step_ms": ms_adj,
             "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms_adj,
                                         "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
@@ -801,7 +809,7 @@ def run_adjoint(a):
                 "config": {"workload": r["workload"], "checkpoint_every": ADJ_EVERY, "repeats": r["repeats"],
                            "forward_steps": r["forward_steps"]},
                 **{k: r[k] for k in ("forward_s", "gradient_s", "gradient_over_forward", "forward_baseline",
-                                     "adjoint_step_ms", "roofline", "clocks")}}
+                                     "other_schedules", "adjoint_step_ms", "roofline", "clocks")}}
         print(json.dumps(line), flush=True)
 
 

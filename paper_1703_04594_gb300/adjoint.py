@@ -8,15 +8,20 @@ the library's hand-written adjoint kernels (``lbm_adjoint_step``, ``lbm_init_adj
 example ``inputs.rt_fields`` with ``modes.a.requires_grad_()``) to get gradients with
 respect to interface-mode amplitudes.
 
-The forward steps (and their recomputation) run in the precision of ``params``: FP64, or
-FP64 with the fixed-point relaxation (LBM_FP64_FIXED, the same states within rounding);
-the adjoint steps are the FP64 ones either way.
+The forward steps run in the precision of ``params``: FP64, or FP64 with the fixed-point
+relaxation (LBM_FP64_FIXED, the same states within rounding); the recomputation runs in
+``recompute_precision`` (default: that of ``params``); the adjoint steps are the FP64 ones
+either way.  Recomputing FP64 states with the fixed-point relaxation (3.1x faster on
+GB300) gives states that agree with the forward pass's to float64 rounding, and the same
+gradient to ~1e-12.
 
 Memory: the forward pass keeps a checkpoint every ``every`` steps (default ceil(sqrt(N)));
 the backward pass recomputes each segment's states from its checkpoint, newest segment
 first, and walks the adjoint back through it.  On a GPU the recomputation of the next
 (earlier) segment runs on a second stream while the adjoint steps of the current one run,
-so the two kernels share the SMs.  Peak: ceil(N/every) + 2 every + 3 states.
+so the two kernels share the SMs.  Peak: ceil(N/every) + 2 every + 2 states.  With
+``every=1`` every state is kept (N + 1 states: 500 steps of 512 x 1024 hold 78 GB of HBM)
+and nothing is recomputed.
 """
 from __future__ import annotations
 
@@ -35,23 +40,35 @@ def default_every(n_steps: int) -> int:
 
 class _KineticEnergyAfter(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, rho, ux, uy, T, tau, params, n_steps, every):
+    def forward(ctx, rho, ux, uy, T, tau, params, n_steps, every, recompute_precision):
         p = dataclasses.replace(params, tau=float(tau))
-        if p.precision not in (lbm.FP64, lbm.FP64_FIXED):
+        if p.precision not in (lbm.FP64, lbm.FP64_FIXED) or recompute_precision not in (lbm.FP64, lbm.FP64_FIXED):
             raise ValueError("the adjoint runs on FP64 states")
         fields = [t.detach().contiguous() for t in (rho, ux, uy, T)]
-        a, b = lbm.empty_state(p, rho.device), lbm.empty_state(p, rho.device)
+        dev = rho.device
+        a = lbm.empty_state(p, dev)
         lbm.init(p, *fields, a)
-        checkpoints = {0: a.clone()}
-        cur, nxt = a, b
+        # each checkpoint is the output buffer of its step (no copy); the other steps
+        # alternate between two working buffers
+        checkpoints = {0: a}
+        kept = {id(a)}
+        free = [lbm.empty_state(p, dev)]
+        cur = a
         for n in range(n_steps):
-            lbm.step(p, cur, nxt)
-            cur, nxt = nxt, cur
-            if (n + 1) % every == 0 and n + 1 < n_steps:
-                checkpoints[n + 1] = cur.clone()
+            keep = (n + 1) % every == 0 and n + 1 < n_steps
+            out = lbm.empty_state(p, dev) if keep or not free else free.pop()
+            lbm.step(p, cur, out)
+            if id(cur) not in kept:
+                free.append(cur)
+            cur = out
+            if keep:
+                checkpoints[n + 1] = out
+                kept.add(id(out))
+        del free
         energy = lbm.kinetic_energy(p, cur)
         ctx.p, ctx.n_steps, ctx.every = p, n_steps, every
-        ctx.checkpoints, ctx.final, ctx.fields = checkpoints, cur.clone(), fields
+        ctx.p_recompute = dataclasses.replace(p, precision=recompute_precision)
+        ctx.checkpoints, ctx.final, ctx.fields = checkpoints, cur, fields
         ctx.tau_shape = tau.shape if torch.is_tensor(tau) else None
         ctx.tau_device = tau.device if torch.is_tensor(tau) else None
         return energy
@@ -75,6 +92,7 @@ class _KineticEnergyAfter(torch.autograd.Function):
             side.wait_stream(main)                         # the checkpoints are ready
         # two pools of every - 1 recomputed states, used by alternate segments: no allocation
         # per step, and a segment is recomputed into the pool the adjoint finished with
+        pr = ctx.p_recompute
         pools = [[lbm.empty_state(p, dev) for _ in range(max(every - 1, 0))] for _ in range(2)]
         released = [None, None]                            # main-stream events: pool free again
 
@@ -87,7 +105,7 @@ class _KineticEnergyAfter(torch.autograd.Function):
                 states = [ctx.checkpoints[k]]
                 for j in range(k, end - 1):
                     nxt = pools[pool][j - k]
-                    lbm.step(p, states[-1], nxt)
+                    lbm.step(pr, states[-1], nxt)
                     states.append(nxt)
                 done = None
                 if cuda:
@@ -114,14 +132,19 @@ class _KineticEnergyAfter(torch.autograd.Function):
         g_tau = None
         if ctx.tau_shape is not None:
             g_tau = dtau.to(ctx.tau_device).reshape(ctx.tau_shape)
-        return g[0], g[1], g[2], g[3], g_tau, None, None, None
+        return g[0], g[1], g[2], g[3], g_tau, None, None, None, None
 
 
-def kinetic_energy_after(rho, ux, uy, T, tau, params: lbm.Params, n_steps: int, every: int | None = None):
+def kinetic_energy_after(rho, ux, uy, T, tau, params: lbm.Params, n_steps: int, every: int | None = None,
+                         recompute_precision: int | None = None):
     """Differentiable total kinetic energy after n_steps FP64 steps (see module docstring).
-    ``tau`` may be a 0-d float64 tensor with requires_grad for dE/dtau."""
+    ``tau`` may be a 0-d float64 tensor with requires_grad for dE/dtau; ``every`` is the
+    checkpoint interval (1 keeps every state); ``recompute_precision`` (LBM_FP64 or
+    LBM_FP64_FIXED) the precision of the backward pass's recomputed steps."""
     if every is None:
         every = default_every(n_steps)
+    if recompute_precision is None:
+        recompute_precision = params.precision
     if not torch.is_tensor(tau):
         tau = torch.tensor(float(tau), dtype=torch.float64)
-    return _KineticEnergyAfter.apply(rho, ux, uy, T, tau, params, int(n_steps), int(every))
+    return _KineticEnergyAfter.apply(rho, ux, uy, T, tau, params, int(n_steps), int(every), int(recompute_precision))

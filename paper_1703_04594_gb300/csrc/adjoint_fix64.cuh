@@ -14,8 +14,11 @@
 // 63 and s^2 62 (as in the forward path).  A product of mu' with a polynomial value keeps
 // the high 64 bits, mu' P / 32; sums over a shell are multiplied by the shell weight w_s
 // (64 fraction bits) and the four results are converted back to float64 with the block
-// exponent.  Each result carries an absolute error of a few units of 2^-55 of
-// max_i |mu_i| w, below the float64 rounding of the same sums.
+// exponent.  The sums' unit is 2^-52 to 2^-51 of max_i |mu_i|; each high product rounds
+// down by less than one unit, half a unit on average, which the sums add back (+1 per
+// two products, +4 for the eight shell products), so a result carries an unbiased error
+// of a few units, comparable to the float64 rounding of the same sums.  (Uncompensated,
+// that bias is the same sign at every site and adds up in dL/dtau.)
 //
 // Range: |c u_s,x|, |c u_s,y| < 0.15 and |t| < 0.25 (as the forward path) and mu finite
 // with max_i |mu_i| in [2^-922, 2^876] (or all zero); other sites use the float64 VJP.
@@ -148,14 +151,22 @@ __device__ __forceinline__ bool eq_vjp_sums_fix(double usx, double usy, double t
     const long long mp = fx_from_double(mu(k), kmu, 64, unused);
     const long long mm = fx_from_double(mu(k + NPAIR), kmu, 64, unused);
     const long long S = mp + mm, Dm = mp - mm;
-    Rs += fx_mulhi(S, E) + fx_mulhi(Dm, O);
-    const long long X = fx_mulhi(Dm, Pse) + fx_mulhi(S, Pso);
+    // each high product rounds down, half a unit low on average: + 1 per two products
+    // (without it the bias, ~2^-51 max|mu| per site, adds up over the sites of dL/dtau)
+    Rs += fx_mulhi(S, E) + fx_mulhi(Dm, O) + 1;
+    const long long X = fx_mulhi(Dm, Pse) + fx_mulhi(S, Pso) + 1;
     Axs += pk.vx * X;
     Ays += pk.vy * X;
-    Ws += fx_mulhi(S, PUe) + fx_mulhi(Dm, PUo);
-    Ts += fx_mulhi(S, Pte) + fx_mulhi(Dm, Pto);
+    Ws += fx_mulhi(S, PUe) + fx_mulhi(Dm, PUo) + 1;
+    Ts += fx_mulhi(S, Pte) + fx_mulhi(Dm, Pto) + 1;
   }
   flush();
+  // the eight shell products of each sum (one per flush) likewise
+  Gr += 4;
+  Ax += 4;
+  Ay += 4;
+  Wu += 4;
+  Gt += 4;
   // mu' P / 32 with mu' = mu 2^kmu: the sums are their values times 2^(kmu - 5)
   const int k = kmu - 5;
   out.Gr = fx_to_double_dp(Gr, k);

@@ -88,3 +88,23 @@ def test_checkpointed_gradient_equals_autograd(monkeypatch, n_steps, every):
 
 def test_default_interval_is_the_square_root():
     assert [A.default_every(n) for n in (1, 4, 5, 500)] == [1, 2, 3, 23]
+
+
+@pytest.mark.parametrize("n_steps,every", [(13, 5), (12, 1), (9, 20)])
+def test_recomputation_precision_and_step_count(monkeypatch, n_steps, every):
+    """Forward steps run in the precision of the params, the backward pass's recomputed
+    steps in ``recompute_precision``; the forward pass takes n_steps steps and the backward
+    pass recomputes every state that is not a checkpoint (none when every = 1)."""
+    B, M = model()
+    lib, _ = fake_library(B, M)
+    calls = []
+    step = lib.step
+    lib.step = lambda p, src, dst: (calls.append(p.precision), step(p, src, dst))[1]
+    monkeypatch.setattr(A, "lbm", lib)
+    xs = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (1.1, 0.02, -0.03, 0.95)]
+    e = A.kinetic_energy_after(*xs, torch.tensor(0.8, dtype=torch.float64), FakeParams(), n_steps, every,
+                               recompute_precision=lib.FP64_FIXED)
+    assert calls == [lib.FP64] * n_steps
+    e.backward()
+    n_checkpoints = len(range(0, n_steps, every))
+    assert calls[n_steps:] == [lib.FP64_FIXED] * (n_steps - n_checkpoints)
