@@ -175,6 +175,18 @@ __device__ __forceinline__ void cp_async8_adj(double* smem_dst, const double* gm
 
 }  // namespace
 
+// The lattice-wide scalars of the adjoint collision, formed once on the host.
+struct AdjConsts {
+  double tau;
+  double om, om2;       // w = 1/tau, w^2
+  double om1;           // 1 - w
+  double om_c, om_c2;   // w c, w c^2
+  double tgx, tgy;      // the gravity shift of the velocity, tau g
+  double tshift;        // tau (1 - tau) |g|^2 / D - 1:  t = T + tshift
+  double gx, gy;
+  double dts_dtau;      // d T_s / d tau = (1 - 2 tau) |g|^2 / D
+};
+
 // Step 1: per-site adjoint of the collision with the transposed propagate as its store
 // (block 32 x 4 as the forward kernels).  `side` holds 2 * lx * kGhostSlots doubles: the
 // bottom slots of every column, then the top slots.
@@ -185,7 +197,7 @@ template <bool PERIODIC>
 __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const double* __restrict__ fin,
                                                      const double* __restrict__ lam_next, double* __restrict__ lam_out,
                                                      double* __restrict__ side, double* __restrict__ dtau_part,
-                                                     StepArgs a, double tau, double gx, double gy) {
+                                                     StepArgs a, AdjConsts k) {
   const int x = blockIdx.y * 4 + threadIdx.y;
   const int y0 = blockIdx.x * 32;
   const int y = y0 + threadIdx.x;
@@ -217,10 +229,9 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
       const double Jx = C * jx, Jy = C * jy, E = C2 * e;  // xi-unit moments
       const double ux = Jx * inv, uy = Jy * inv;
       const double uu = fma(ux, ux, uy * uy);
-      const double T = (E * inv - uu) / D;
-      const double gg = fma(gx, gx, gy * gy);
-      const double usx = fma(tau, gx, ux), usy = fma(tau, gy, uy);
-      const double t = T + tau * (1.0 - tau) * gg / D - 1.0;
+      const double TD = fma(E, inv, -uu);  // D T
+      const double usx = ux + k.tgx, usy = uy + k.tgy;
+      const double t = fma(TD, 1.0 / D, k.tshift);
       const long long o = (long long)x * a.pitch + y;
       const double* lam = lam_next + o;
       // sum_i mu_i f~_i; each staging slot, once its f~_i is read, takes mu_i = lambda_i, so
@@ -235,22 +246,30 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
         sf[i * 32] = l;
       }
       const auto mu = [&](int i) { return sf[i * 32]; };
-      // the VJP in fixed point (adjoint_fix64.cuh), in float64 outside its range
-      EqVjp G;
-      VjpSums V;
-      if (eq_vjp_sums_fix(usx, usy, t, mu, V)) {
-        G.Grho = V.Gr;
-        G.Gux = rho * fma(C, V.Ax, 2.0 * usx * V.Wu);
-        G.Guy = rho * fma(C, V.Ay, 2.0 * usy * V.Wu);
-        G.Gt = rho * V.Gt;
-      } else {
-        G = eq_vjp_float64(rho, usx, usy, t, sf);
+      // the VJP in fixed point (adjoint_fix64.cuh), in float64 outside its range, per unit
+      // density: g = G / rho for G_u and G_t (G_rho has no factor rho)
+      double gr, gux, guy, gt;
+      {
+        VjpSums V;
+        if (eq_vjp_sums_fix(usx, usy, t, mu, V)) {
+          gr = V.Gr;
+          gux = fma(C, V.Ax, 2.0 * usx * V.Wu);
+          guy = fma(C, V.Ay, 2.0 * usy * V.Wu);
+          gt = V.Gt;
+        } else {
+          const EqVjp G = eq_vjp_float64(1.0, usx, usy, t, sf);
+          gr = G.Grho;
+          gux = G.Gux;
+          guy = G.Guy;
+          gt = G.Gt;
+        }
       }
-      const double nuE = G.Gt * inv / D;
-      const double nuJx = G.Gux * inv - 2.0 * ux * G.Gt * inv / D;
-      const double nuJy = G.Guy * inv - 2.0 * uy * G.Gt * inv / D;
-      const double nuR = G.Grho - (G.Gux * ux + G.Guy * uy) * inv + G.Gt * (-E * inv + 2.0 * uu) * inv / D;
-      const double om = 1.0 / tau, om1 = 1.0 - om;
+      // nu = (d f^eq / d(rho, J, E))^T mu through u = J / rho, T = (E / rho - |u|^2) / D:
+      // the factors rho of G and 1 / rho of the chain rule cancel, and E / rho = D T + |u|^2
+      const double nuE = gt * (1.0 / D);
+      const double nuJx = fma(-2.0 * ux, nuE, gux);
+      const double nuJy = fma(-2.0 * uy, nuE, guy);
+      const double nuR = fma(nuE, uu - TD, gr - fma(gux, ux, guy * uy));
       // out_i(z) is lambda_i(z - v_i) of the previous step (the transposed pull), or the
       // wall slot of its source column when z - v_i is a ghost
       // (the destination is selected, not branched on, to keep the kernel's code small)
@@ -271,15 +290,16 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
       };
       // out_{+-v} = (1-w) mu + A_s +- B_v with A_s = w (nuR + nuE c^2 |v|^2) (one per shell)
       // and B_v = w c nuJ . v (from the multiples of w c nuJ)
-      const double wR = om * nuR, wE = om * (C2 * nuE);
-      const Multiples wJ = make_multiples(om * (C * nuJx), om * (C * nuJy));
+      const double om1 = k.om1;
+      const double wR = k.om * nuR, wE = k.om_c2 * nuE;
+      const Multiples wJ = make_multiples(k.om_c * nuJx, k.om_c * nuJy);
       push(0, fma(om1, mu(0), wR));
 #pragma unroll
-      for (int k = 1; k <= NPAIR; ++k) {
-        const double A = fma(wE, (double)v2(k), wR);
-        const double B = dot_v(wJ, rep_vx(k), rep_vy(k));
-        push(k, fma(om1, mu(k), A + B));
-        push(k + NPAIR, fma(om1, mu(k + NPAIR), A - B));
+      for (int j = 1; j <= NPAIR; ++j) {
+        const double A = fma(wE, (double)v2(j), wR);
+        const double B = dot_v(wJ, rep_vx(j), rep_vy(j));
+        push(j, fma(om1, mu(j), A + B));
+        push(j + NPAIR, fma(om1, mu(j + NPAIR), A - B));
       }
       // entries of this site whose source z + v_i lies beyond a wall get no push
       if (!PERIODIC && (y < 3 || y >= a.ly - 3)) {
@@ -290,7 +310,7 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
         }
       }
       // sum_i mu_i f^eq_i = rho * Grho
-      contrib = -(rho * G.Grho - mu_ft) * om * om + om * (G.Gux * gx + G.Guy * gy + G.Gt * (1.0 - 2.0 * tau) * gg / D);
+      contrib = fma(-k.om2, fma(rho, gr, -mu_ft), (k.om * rho) * fma(gux, k.gx, fma(guy, k.gy, gt * k.dts_dtau)));
     }
   }
   const double s = block_sum_128(contrib);
@@ -388,10 +408,24 @@ long long adjoint_side_count(const StepArgs& a) { return 2LL * a.lx * kGhostSlot
 cudaError_t launch_adjoint_step(const double* fin, const double* lam_next, double* lam, double* side, double* part,
                                 double* dtau, const StepArgs& a, double tau, double gx, double gy, cudaStream_t s) {
   const dim3 blk(32, 4);
+  AdjConsts k;
+  k.tau = tau;
+  k.om = 1.0 / tau;
+  k.om2 = k.om * k.om;
+  k.om1 = 1.0 - k.om;
+  k.om_c = k.om * C;
+  k.om_c2 = k.om * C2;
+  k.tgx = tau * gx;
+  k.tgy = tau * gy;
+  const double gg = gx * gx + gy * gy;
+  k.tshift = tau * (1.0 - tau) * gg / D - 1.0;
+  k.gx = gx;
+  k.gy = gy;
+  k.dts_dtau = (1.0 - 2.0 * tau) * gg / D;
   if (a.periodic) {
-    k_adj_collide<true><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, tau, gx, gy);
+    k_adj_collide<true><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, k);
   } else {
-    k_adj_collide<false><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, tau, gx, gy);
+    k_adj_collide<false><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, k);
     k_adj_walls<<<dim3((a.lx + 127) / 128, 2), 128, 0, s>>>(side, lam, a);
   }
   k_reduce_add<<<1, 256, 0, s>>>(part, adjoint_partial_count(a), dtau);
