@@ -63,7 +63,7 @@ TRAFFIC_BYTES_PER_SITE = {
     "fp64fix": 569.2,      # k_step_fix64, 1024 x 2048
     "fp32": 272.8,         # k_step_fp32 (shifted), 1024 x 2048
     "fp32c": 273.3,        # k_step_fp32 (conserved moments), 1024 x 2048
-    "adjoint": None,       # k_adj_collide changed since its last capture
+    "adjoint": 830.3,      # k_adj_collide, 512 x 1024 (the adjoint workload's own lattice)
     "batch_fp32": 259.4,   # k_batch_step<fp32>, 64 small lattices
     "batch_fp64": 587.2,   # k_batch_step<double>, 8 lattices Lx 128..1024
     "separate": None,
