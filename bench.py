@@ -196,9 +196,10 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_sample(steps: int, cols: int = 16):
+def oracle_sample(steps: int, cols: int = 16, threads: int | None = None):
     """Time the float64 CPU oracle on a bounded crop of the same workload: ``cols`` full-
-    height columns (cols x 8192 sites) of the seed-2 Rayleigh-Taylor lattice."""
+    height columns (cols x 8192 sites) of the seed-2 Rayleigh-Taylor lattice, on torch's
+    default thread count or on ``threads`` threads."""
     import torch
 
     from oracle import lbm as OL
@@ -208,11 +209,18 @@ def oracle_sample(steps: int, cols: int = 16):
     fields = [t[:cols].contiguous() for t in I.rt_fields(LX, LY, modes, T_BOTTOM, T_TOP, abs(GY))]
     p = OL.Params(cols, LY, tau=TAU, gy=GY, t_bottom=T_BOTTOM, t_top=T_TOP)
     f = OL.init_equilibrium(*fields)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        f = OL.step(f, p)
-    dt = time.perf_counter() - t0
-    return {"value": cols * LY * steps / dt / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
+    saved = torch.get_num_threads()
+    if threads is not None:
+        torch.set_num_threads(threads)
+    try:
+        used = torch.get_num_threads()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            f = OL.step(f, p)
+        dt = time.perf_counter() - t0
+    finally:
+        torch.set_num_threads(saved)
+    return {"value": cols * LY * steps / dt / 1e6, "unit": "MLUPS", "cores": used,
             "kind": "oracle",
             "sample": f"{cols}x{LY} column crop of the {LX}x{LY} seed-{SEED} RT lattice, {steps} steps, "
                       f"{dt:.1f} s"}
@@ -434,6 +442,8 @@ def run_ours(a):
                 "clocks": clk.summary()}
         if not a.no_cpu_baseline and world == 1 and (lx, ly) == (LX, LY):
             line["cpu_baseline"] = oracle_sample(16)   # ~14 s of CPU work on 16 cores
+            # the same oracle on one thread, on a smaller crop (~5 s)
+            line["cpu_baseline"]["single_thread"] = oracle_sample(4, cols=2, threads=1)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
