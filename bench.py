@@ -727,7 +727,7 @@ def run_adjoint_step(a):
                       "higher_is_better": True, "dtype": "f64+i64", "data": "synthetic",
                       "config": {"workload": f"lbm_adjoint_step on a {lx}x{ly} RT state"},
                       "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms,
-                                                  "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
+                                                  "lbm_adjoint_step (k_adj_collide, then k_adj_walls with the fixed-order dL/dtau sum)",
                                                   traffic("adjoint", sites)),
                       "clocks": clk}), flush=True)
 
@@ -747,8 +747,10 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
                    precision=lbm.FP64_FIXED if precision == "fp64fix" else lbm.FP64)
     modes = I.rt_modes(lx, ly, seed)
 
+    # the fields are built on the device in both runs (the same torch operations; the
+    # gradient's backward pass through them then runs there too)
     def forward_only():
-        fields = [t.contiguous().cuda() for t in I.rt_fields(lx, ly, modes, T_BOTTOM, T_TOP, abs(GY))]
+        fields = [t.contiguous() for t in I.rt_fields(lx, ly, modes, T_BOTTOM, T_TOP, abs(GY), device="cuda")]
         f = lbm.empty_state(p)
         lbm.init(p, *fields, f)
         res = lbm.run(p, f, lbm.empty_state(p), n)
@@ -757,8 +759,8 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
     def gradient(every=every, recompute=None):
         amp = modes.a.clone().requires_grad_(True)
         tau = torch.tensor(TAU, dtype=torch.float64, requires_grad=True)
-        fields = I.rt_fields(lx, ly, I.RTModes(a=amp, phi=modes.phi), T_BOTTOM, T_TOP, abs(GY))
-        e = A.kinetic_energy_after(*[t.cuda() for t in fields], tau, p, n, every, recompute_precision=recompute)
+        fields = I.rt_fields(lx, ly, I.RTModes(a=amp, phi=modes.phi), T_BOTTOM, T_TOP, abs(GY), device="cuda")
+        e = A.kinetic_energy_after(*[t.contiguous() for t in fields], tau, p, n, every, recompute_precision=recompute)
         e.backward()
         return amp.grad, tau.grad
 
@@ -797,7 +799,7 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
             "other_schedules": schedules,
             "adjoint_step_ms": ms_adj,
             "roofline": kernel_roofline("hbm", BYTES_PER_SITE_ADJ, sites, ms_adj,
-                                        "lbm_adjoint_step (k_adj_collide + k_adj_walls + k_reduce_add)",
+                                        "lbm_adjoint_step (k_adj_collide, then k_adj_walls with the fixed-order dL/dtau sum)",
                                         traffic("adjoint", sites)),
             "clocks": clk.summary(), "adjoint_step_clocks": aclk}
 

@@ -19,7 +19,9 @@ Memory: the forward pass keeps a checkpoint every ``every`` steps (default ceil(
 the backward pass recomputes each segment's states from its checkpoint, newest segment
 first, and walks the adjoint back through it.  On a GPU the recomputation of the next
 (earlier) segment runs on a second stream while the adjoint steps of the current one run,
-so the two kernels share the SMs.  Peak: ceil(N/every) + 2 every + 2 states.  With
+so the two kernels share the SMs.  The states after the newest checkpoint are kept from
+the forward pass, so the newest segment is not recomputed.  Peak: ceil(N/every) + 2 every
++ 2 states.  With
 ``every=1`` every state is kept (N + 1 states: 500 steps of 512 x 1024 hold 78 GB of HBM)
 and nothing is recomputed.
 """
@@ -48,24 +50,32 @@ class _KineticEnergyAfter(torch.autograd.Function):
         dev = rho.device
         a = lbm.empty_state(p, dev)
         lbm.init(p, *fields, a)
-        # each checkpoint is the output buffer of its step (no copy); the other steps
-        # alternate between two working buffers
+        # each checkpoint is the output buffer of its step (no copy); so are the states after
+        # the newest checkpoint (the tail), which the backward pass needs first and so need
+        # not recompute; the other steps alternate between two working buffers
+        last = ((n_steps - 1) // every) * every if n_steps > 0 else 0
+        tail = [lbm.empty_state(p, dev) for _ in range(max(n_steps - last - 1, 0))]
         checkpoints = {0: a}
-        kept = {id(a)}
+        kept = {id(a)} | {id(t) for t in tail}
         free = [lbm.empty_state(p, dev)]
         cur = a
         for n in range(n_steps):
-            keep = (n + 1) % every == 0 and n + 1 < n_steps
-            out = lbm.empty_state(p, dev) if keep or not free else free.pop()
+            m = n + 1                                      # the state this step produces
+            keep = m % every == 0 and m < n_steps
+            if last < m < n_steps:
+                out = tail[m - last - 1]
+            else:
+                out = lbm.empty_state(p, dev) if keep or not free else free.pop()
             lbm.step(p, cur, out)
             if id(cur) not in kept:
                 free.append(cur)
             cur = out
             if keep:
-                checkpoints[n + 1] = out
+                checkpoints[m] = out
                 kept.add(id(out))
         del free
         energy = lbm.kinetic_energy(p, cur)
+        ctx.tail = tail
         ctx.p, ctx.n_steps, ctx.every = p, n_steps, every
         ctx.p_recompute = dataclasses.replace(p, precision=recompute_precision)
         ctx.checkpoints, ctx.final, ctx.fields = checkpoints, cur, fields
@@ -75,9 +85,31 @@ class _KineticEnergyAfter(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_e):
+        dev = ctx.final.device
+        if dev.type != "cuda":
+            return _KineticEnergyAfter._backward(ctx, grad_e, dev, None, None)
+        # the adjoint steps run on a stream of higher priority than the recomputation's:
+        # while an adjoint launch has blocks waiting they go first, and the recomputed
+        # steps fill the SMs its last wave leaves idle
+        caller = torch.cuda.current_stream(dev)
+        adj = torch.cuda.Stream(dev, priority=-1)
+        side = torch.cuda.Stream(dev)
+        adj.wait_stream(caller)                            # the checkpoints are ready
+        side.wait_stream(caller)
+        with torch.cuda.stream(adj):
+            out = _KineticEnergyAfter._backward(ctx, grad_e, dev, adj, side)
+        caller.wait_stream(adj)
+        for t in out[:4]:
+            t.record_stream(caller)
+        return out
+
+    @staticmethod
+    def _backward(ctx, grad_e, dev, main, side):
+        """The backward pass; `main` (the current stream) takes the adjoint steps, `side` the
+        recomputation (both None on the CPU)."""
         p, n_steps, every = ctx.p, ctx.n_steps, ctx.every
         pa = dataclasses.replace(p, precision=lbm.FP64)  # the adjoint kernels (same states)
-        dev = ctx.final.device
+        cuda = main is not None
         lam = lbm.empty_state(pa, dev)
         lbm.kinetic_energy_grad(pa, ctx.final, lam)
         lam.mul_(grad_e.to(dev))
@@ -85,15 +117,19 @@ class _KineticEnergyAfter(torch.autograd.Function):
         dtau = torch.zeros((), dtype=torch.float64, device=dev)
         work = lbm.adjoint_work(pa, dev)
         order = sorted(ctx.checkpoints, reverse=True)      # newest segment first
-        cuda = dev.type == "cuda"
-        main = torch.cuda.current_stream(dev) if cuda else None
-        side = torch.cuda.Stream(dev) if cuda else None
-        if cuda:
-            side.wait_stream(main)                         # the checkpoints are ready
         # two pools of every - 1 recomputed states, used by alternate segments: no allocation
         # per step, and a segment is recomputed into the pool the adjoint finished with
         pr = ctx.p_recompute
-        pools = [[lbm.empty_state(p, dev) for _ in range(max(every - 1, 0))] for _ in range(2)]
+        # pool 0 starts as the forward pass's tail: the newest segment is not recomputed
+        tail, ctx.tail = ctx.tail, None
+        pools = [tail + [lbm.empty_state(p, dev) for _ in range(max(every - 1 - len(tail), 0))],
+                 [lbm.empty_state(p, dev) for _ in range(max(every - 1, 0))]]
+        if cuda:
+            # buffers used on a stream other than their allocating one: the allocator must not
+            # reuse them before that stream's work on them is done
+            for t in list(ctx.checkpoints.values()) + pools[0] + pools[1]:
+                t.record_stream(main)
+                t.record_stream(side)
         released = [None, None]                            # main-stream events: pool free again
 
         def recompute(k, pool):
@@ -113,10 +149,12 @@ class _KineticEnergyAfter(torch.autograd.Function):
                     done.record(side)
             return k, end, states, done
 
-        pending = recompute(order[0], 0)
+        k0 = order[0]
+        end0 = min(k0 + every, n_steps)
+        pending = (k0, end0, [ctx.checkpoints[k0]] + tail[: end0 - k0 - 1], None)
         for idx in range(len(order)):
             k, end, states, done = pending
-            if cuda:
+            if cuda and done is not None:
                 main.wait_event(done)
             if idx + 1 < len(order):
                 pending = recompute(order[idx + 1], (idx + 1) % 2)   # overlaps the adjoint steps below

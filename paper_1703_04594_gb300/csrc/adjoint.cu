@@ -317,13 +317,35 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
   if (threadIdx.x == 0 && threadIdx.y == 0) dtau_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
+// Adds sum(part[0..n)) to *acc in a fixed order; one block of 256 threads.
+__device__ __forceinline__ void reduce_add_256(const double* __restrict__ part, long long n, double* acc) {
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += 256) s += part[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    *acc += t;
+  }
+}
+
 // Step 2: the wall rows' share of the transposed bc, after step 1 has written every
 // lambda entry: lambda_j(x, 0) += sum over the bottom slots of column x of the slot's value
 // times its ghost's weight w_i P_i(T_bottom), for all j (the ghost values' dependence on
 // rho_w(x) = sum_j f_j(x, 0)), and likewise for row ly - 1.  One thread per column and
-// wall (blockIdx.y: 0 bottom, 1 top).
-__global__ void __launch_bounds__(128) k_adj_walls(const double* __restrict__ side, double* __restrict__ lam,
-                                                   StepArgs a) {
+// wall (blockIdx.y: 0 bottom, 1 top); block (0, 2) adds the step's dL/dtau partials to
+// *dtau (the reduction needs step 1 complete too, so it shares this launch).
+__global__ void __launch_bounds__(256) k_adj_walls(const double* __restrict__ side, double* __restrict__ lam,
+                                                   StepArgs a, const double* __restrict__ part, long long n_part,
+                                                   double* dtau) {
+  if (blockIdx.y == 2) {
+    if (blockIdx.x == 0) reduce_add_256(part, n_part, dtau);
+    return;
+  }
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= a.lx) return;
   const int top = blockIdx.y;
@@ -345,20 +367,9 @@ __global__ void __launch_bounds__(128) k_adj_walls(const double* __restrict__ si
   for (int i = 0; i < Q; ++i) dst[i * a.pop] += wall;
 }
 
-// Adds sum(part[0..n)) to *acc in a fixed order (one block).
+// Adds sum(part[0..n)) to *acc in a fixed order (one block of 256 threads).
 __global__ void __launch_bounds__(256) k_reduce_add(const double* __restrict__ part, long long n, double* acc) {
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  __shared__ double ws[8];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += ws[w];
-    *acc += t;
-  }
+  reduce_add_256(part, n, acc);
 }
 
 // dE/df_i for E = sum 1/2 |J|^2 / rho:  -|u|^2/2 + u . xi_i.
@@ -426,7 +437,8 @@ cudaError_t launch_adjoint_step(const double* fin, const double* lam_next, doubl
     k_adj_collide<true><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, k);
   } else {
     k_adj_collide<false><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, k);
-    k_adj_walls<<<dim3((a.lx + 127) / 128, 2), 128, 0, s>>>(side, lam, a);
+    k_adj_walls<<<dim3((a.lx + 255) / 256, 3), 256, 0, s>>>(side, lam, a, part, adjoint_partial_count(a), dtau);
+    return cudaGetLastError();
   }
   k_reduce_add<<<1, 256, 0, s>>>(part, adjoint_partial_count(a), dtau);
   return cudaGetLastError();

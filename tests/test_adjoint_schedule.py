@@ -94,7 +94,8 @@ def test_default_interval_is_the_square_root():
 def test_recomputation_precision_and_step_count(monkeypatch, n_steps, every):
     """Forward steps run in the precision of the params, the backward pass's recomputed
     steps in ``recompute_precision``; the forward pass takes n_steps steps and the backward
-    pass recomputes every state that is not a checkpoint (none when every = 1)."""
+    pass recomputes every state that is neither a checkpoint nor after the newest
+    checkpoint (those the forward pass keeps); none when every = 1."""
     B, M = model()
     lib, _ = fake_library(B, M)
     calls = []
@@ -107,4 +108,6 @@ def test_recomputation_precision_and_step_count(monkeypatch, n_steps, every):
     assert calls == [lib.FP64] * n_steps
     e.backward()
     n_checkpoints = len(range(0, n_steps, every))
-    assert calls[n_steps:] == [lib.FP64_FIXED] * (n_steps - n_checkpoints)
+    newest = ((n_steps - 1) // every) * every
+    n_tail = n_steps - newest - 1
+    assert calls[n_steps:] == [lib.FP64_FIXED] * (n_steps - n_checkpoints - n_tail)
