@@ -764,26 +764,33 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
         e.backward()
         return amp.grad, tau.grad
 
-    def timed(fn):
-        fn()
+    def one(fn):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(repeats):
-            fn()
+        fn()
         torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / repeats
+        return time.perf_counter() - t0
 
+    def timed_against_forward(fn):
+        """Mean times of fn and of the forward run, the two alternated `repeats` times (so
+        that a drift of the GPU's speed over the run cancels in their ratio)."""
+        fn()
+        forward_only()
+        tf = tg = 0.0
+        for _ in range(repeats):
+            tf += one(forward_only)
+            tg += one(fn)
+        return tg / repeats, tf / repeats
+
+    # the default schedule, and the same gradient under two others: the segments recomputed
+    # with the float64 step (the default recomputes them with the fixed-point relaxation),
+    # and every state kept in HBM (no recomputation)
     with ClockSampler(0) as clk:
-        t_fwd = timed(forward_only)
-        t_grad = timed(gradient)
-    # the same gradient under the two other schedules: the segments recomputed with the
-    # fixed-point relaxation, and every state kept in HBM (no recomputation)
-    other = {}
-    if precision != "fp64fix":
-        other["fixed_point_recomputation"] = timed(lambda: gradient(recompute=lbm.FP64_FIXED))
-    other["every_state_kept"] = timed(lambda: gradient(every=1))
+        t_grad, t_fwd = timed_against_forward(gradient)
+    other = {"float64_recomputation": timed_against_forward(lambda: gradient(recompute=lbm.FP64)),
+             "every_state_kept": timed_against_forward(lambda: gradient(every=1))}
     torch.cuda.empty_cache()
-    schedules = {k: {"gradient_s": v, "gradient_over_forward": v / t_fwd} for k, v in other.items()}
+    schedules = {k: {"gradient_s": g, "forward_s": f, "gradient_over_forward": g / f} for k, (g, f) in other.items()}
     schedules["every_state_kept"]["memory_gb"] = (n + 1) * lbm.buffer_bytes(p) / 1e9
     ms_adj, aclk = adjoint_step_ms(lx, ly, modes, warmup=4, calls=40)
     sites = lx * ly
@@ -793,6 +800,7 @@ def adjoint_form(a, repeats, precision="fp64", seed=5):
             "workload": f"dE/d(a_1..a_8, tau), E = kinetic energy after {n} steps of {lx}x{ly}, checkpoints "
                         f"every {every}", "repeats": repeats,
             "forward_steps": "fixed-point relaxation" if precision == "fp64fix" else "float64",
+            "recomputed_steps": "fixed-point relaxation",
             "gradient_s": t_grad, "forward_s": t_fwd, "gradient_over_forward": t_grad / t_fwd,
             "forward_baseline": {"value": whole_job_mlups(sites, n, 1, t_fwd * 1e3), "unit": "MLUPS",
                                  "what": "the same 500 forward steps and the energy, no gradient"},
@@ -819,7 +827,7 @@ def run_adjoint(a):
                 "vs_baseline": None, "dtype": "f64+i64" if a.precision == "fp64fix" else "f64",
                 "data": "synthetic",
                 "config": {"workload": r["workload"], "checkpoint_every": ADJ_EVERY, "repeats": r["repeats"],
-                           "forward_steps": r["forward_steps"]},
+                           "forward_steps": r["forward_steps"], "recomputed_steps": r["recomputed_steps"]},
                 **{k: r[k] for k in ("forward_s", "gradient_s", "gradient_over_forward", "forward_baseline",
                                      "other_schedules", "adjoint_step_ms", "roofline", "clocks")}}
         print(json.dumps(line), flush=True)

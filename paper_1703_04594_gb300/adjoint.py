@@ -9,11 +9,13 @@ example ``inputs.rt_fields`` with ``modes.a.requires_grad_()``) to get gradients
 respect to interface-mode amplitudes.
 
 The forward steps run in the precision of ``params``: FP64, or FP64 with the fixed-point
-relaxation (LBM_FP64_FIXED, the same states within rounding); the recomputation runs in
-``recompute_precision`` (default: that of ``params``); the adjoint steps are the FP64 ones
-either way.  Recomputing FP64 states with the fixed-point relaxation (3.1x faster on
-GB300) gives states that agree with the forward pass's to float64 rounding, and the same
-gradient to ~1e-12.
+relaxation (LBM_FP64_FIXED, the same states within rounding), so the energy is that of the
+plain forward run bit for bit; the recomputation runs in ``recompute_precision``, by
+default the fixed-point relaxation (3.1x faster on GB300 than the float64 step): the
+recomputed states are only the points the adjoint linearises at, and they agree with the
+forward pass's to float64 rounding (the gradient agrees with a float64 recomputation's
+to ~1e-12).  ``recompute_precision=LBM_FP64`` recomputes with the float64 step; the
+adjoint steps are the FP64 ones either way.
 
 Memory: the forward pass keeps a checkpoint every ``every`` steps (default ceil(sqrt(N)));
 the backward pass recomputes each segment's states from its checkpoint, newest segment
@@ -177,12 +179,12 @@ def kinetic_energy_after(rho, ux, uy, T, tau, params: lbm.Params, n_steps: int, 
                          recompute_precision: int | None = None):
     """Differentiable total kinetic energy after n_steps FP64 steps (see module docstring).
     ``tau`` may be a 0-d float64 tensor with requires_grad for dE/dtau; ``every`` is the
-    checkpoint interval (1 keeps every state); ``recompute_precision`` (LBM_FP64 or
-    LBM_FP64_FIXED) the precision of the backward pass's recomputed steps."""
+    checkpoint interval (1 keeps every state); ``recompute_precision`` (LBM_FP64_FIXED,
+    the default, or LBM_FP64) the precision of the backward pass's recomputed steps."""
     if every is None:
         every = default_every(n_steps)
     if recompute_precision is None:
-        recompute_precision = params.precision
+        recompute_precision = lbm.FP64_FIXED
     if not torch.is_tensor(tau):
         tau = torch.tensor(float(tau), dtype=torch.float64)
     return _KineticEnergyAfter.apply(rho, ux, uy, T, tau, params, int(n_steps), int(every), int(recompute_precision))

@@ -110,10 +110,10 @@ def reach_max(m, bc):
 def test_adjoint_step_matches_oracle_vjp(kind, bc):
     """One adjoint step against autograd through the oracle's step, per element.
     'rt': a Rayleigh-Taylor state; 'hot_fast': temperatures up to 1.38 and a drift of
-    c u ~ 0.2, so that sites leave the fixed-point range of the VJP and of the outputs
-    (t > 0.25, |c u_s| > 0.15) and take the float64 path, mixed with in-range sites within
-    a warp; 'wide_lambda': lambda scaled per site by 10^U(-6, 3), so that the block
-    fixed-point outputs of a small site next to large ones are checked against the largest
+    c u ~ 0.2, so that sites leave the fixed-point range of the VJP (t > 0.25,
+    |c u_s| > 0.15) and take the float64 path, mixed with in-range sites within a warp;
+    'wide_lambda': lambda scaled per site by 10^U(-6, 3), so that the outputs of a small
+    site next to large ones (its VJP in block fixed point) are checked against the largest
     lambda within its reach, not against the lattice maximum."""
     p = lbm.Params(20, 40, tau=0.7, gx=1e-4, gy=-2e-4, bc=bc)
     rho, ux, uy, T = rt_fields(p, seed=11)
@@ -210,11 +210,11 @@ def test_gradient_matches_finite_differences_512x1024_500_steps():
 
 def test_fixed_point_recomputation_gives_the_same_gradient():
     """FP64 forward steps with the backward pass's segments recomputed by the fixed-point
-    relaxation: the same energy (the forward pass is the FP64 one) and the same gradient
-    within 1e-9."""
+    relaxation (the default) against the float64 recomputation: the same energy (the
+    forward pass is the FP64 one) and the same gradient within 1e-9."""
     args = (64, 128, 4, 0.8, 40)
-    e0, ga0, gt0 = gpu_energy_and_grad(*args, every=7)
-    e1, ga1, gt1 = gpu_energy_and_grad(*args, every=7, recompute_precision=lbm.FP64_FIXED)
+    e0, ga0, gt0 = gpu_energy_and_grad(*args, every=7, recompute_precision=lbm.FP64)
+    e1, ga1, gt1 = gpu_energy_and_grad(*args, every=7)
     assert e1 == e0
     assert float((ga1 - ga0).abs().max()) <= 1e-9 * float(ga0.abs().max())
     assert abs(gt1 - gt0) <= 1e-9 * abs(gt0)
@@ -222,9 +222,10 @@ def test_fixed_point_recomputation_gives_the_same_gradient():
 
 def test_every_state_kept_gives_the_same_gradient():
     """every = 1 keeps every state and recomputes none: the adjoint steps see the same
-    states in the same order, so the gradient is bit for bit that of every = 7."""
+    states in the same order, so the gradient is bit for bit that of every = 7 with the
+    float64 recomputation."""
     args = (64, 128, 4, 0.8, 40)
-    e0, ga0, gt0 = gpu_energy_and_grad(*args, every=7)
+    e0, ga0, gt0 = gpu_energy_and_grad(*args, every=7, recompute_precision=lbm.FP64)
     e1, ga1, gt1 = gpu_energy_and_grad(*args, every=1)
     assert e1 == e0
     assert torch.equal(ga1, ga0)
