@@ -101,34 +101,59 @@ __device__ __noinline__ void wall_strip_fp64(const double* __restrict__ fin, dou
   step_strip_fp64<PERIODIC>(fin, fout, a, w, x, y0, Ld());
 }
 
+// Whether the strip at rows y0 .. y0 + 31 runs the float64 wall strip (its pulls reach a
+// ghost row).
+template <bool PERIODIC>
+__device__ __forceinline__ bool fix64_wall_strip(const StepScalars& a, int y0) {
+  return !PERIODIC && (y0 < 3 || y0 + 32 > a.ly - 3);
+}
+
+// 1. The pull-gather of an interior strip into its shared-memory slots sf[i * 32 + lane]:
+// asynchronous copies when Ld caches in L1 (the caller waits for them), loads otherwise.
+template <bool PERIODIC, class Ld>
+__device__ __forceinline__ void stage_strip_fix64(const double* __restrict__ fin, const StepScalars& a, int x, int y0,
+                                                  Ld ld, double* __restrict__ sf) {
+  const int lane = threadIdx.x & 31;
+  const int y = y0 + lane;
+  const int yc = y < a.ly ? y : a.ly - 1;
+  unsigned off[7];  // column x_s, row yc within a population plane (planes < 2^32 elements)
+#pragma unroll
+  for (int d = 0; d < 7; ++d) off[d] = (unsigned)((long long)wrap_index(x - (d - 3), a.lx) * a.pitch + yc);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double* src = PERIODIC ? fin + i * a.pop + (off[vx(i) + 3] - yc) + wrap_index(yc - vy(i), a.ly)
+                                 : fin + i * a.pop + (off[vx(i) + 3] - vy(i));
+    if (Ld::kL1) cp_async8(sf + i * 32 + lane, src);
+    else sf[i * 32 + lane] = ld(src);
+  }
+}
+
+template <bool PERIODIC, class Ld>
+__device__ __forceinline__ void compute_strip_fix64(const double* __restrict__ fin, double* __restrict__ fout,
+                                                    const StepScalars& a, int x, int y0, double* __restrict__ sf);
+
 template <bool PERIODIC, class Ld>
 __device__ __forceinline__ void step_strip_fix64(const double* __restrict__ fin, double* __restrict__ fout,
                                                  const StepScalars& a, const StepWalls& w, int x, int y0, Ld ld,
                                                  double* __restrict__ sf) {
-  const bool wall_warp = !PERIODIC && (y0 < 3 || y0 + 32 > a.ly - 3);
-  if (wall_warp) {
+  if (fix64_wall_strip<PERIODIC>(a, y0)) {
     wall_strip_fp64<PERIODIC, Ld>(fin, fout, a, w, x, y0);
     return;
   }
+  stage_strip_fix64<PERIODIC>(fin, a, x, y0, ld, sf);
+  if (Ld::kL1) cp_async_wait_all();
+  __syncwarp();
+  compute_strip_fix64<PERIODIC, Ld>(fin, fout, a, x, y0, sf);
+}
+
+// 2.-4. The collision of an interior strip from its staged populations.
+template <bool PERIODIC, class Ld>
+__device__ __forceinline__ void compute_strip_fix64(const double* __restrict__ fin, double* __restrict__ fout,
+                                                    const StepScalars& a, int x, int y0, double* __restrict__ sf) {
   const int lane = threadIdx.x & 31;
   const int y = y0 + lane;
   const bool active = y < a.ly;
   const int yc = active ? y : a.ly - 1;
-  // 1. stage the pull-gather in shared memory
-  {
-    unsigned off[7];  // column x_s, row yc within a population plane (planes < 2^32 elements)
-#pragma unroll
-    for (int d = 0; d < 7; ++d) off[d] = (unsigned)((long long)wrap_index(x - (d - 3), a.lx) * a.pitch + yc);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const double* src = PERIODIC ? fin + i * a.pop + (off[vx(i) + 3] - yc) + wrap_index(yc - vy(i), a.ly)
-                                   : fin + i * a.pop + (off[vx(i) + 3] - vy(i));
-      if (Ld::kL1) cp_async8(sf + i * 32 + lane, src);
-      else sf[i * 32 + lane] = ld(src);
-    }
-    if (Ld::kL1) cp_async_wait_all();
-    __syncwarp();
-  }
   sf += lane;
   long long* const sx = reinterpret_cast<long long*>(sf);  // the same slots, as fixed point
   // 2. every population to fixed point f' = f 2^(59 + e_s), written back in place, and the
