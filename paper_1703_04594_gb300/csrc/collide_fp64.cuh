@@ -22,6 +22,21 @@
 
 namespace d2q37 {
 
+// x * 2^k as an integer addition to x's exponent field: GB300 runs float64 at 1/64 of its
+// float32 rate, and these kernels are bound by that pipe, so the exact scalings by powers
+// of two move to the integer pipe.  The result equals the float64 product bit for bit when
+// x and the result are normal.  Zeros, subnormals, infinities and NaNs are returned
+// unchanged, and a result below the normal range becomes a zero of x's sign; neither case
+// arises from a valid state (|k| <= 52 and the values scaled here are far inside the
+// normal range, never near its top).
+__device__ __forceinline__ double pow2_scale(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const long long sign = b & (long long)0x8000000000000000ull;
+  const long long scaled = e + k > 0 ? b + ((long long)k << 52) : sign;
+  return __longlong_as_double(e == 0 || e == 0x7ff ? b : scaled);
+}
+
 struct CollideConst {
   double omega;   // 1 / tau
   double om1;     // 1 - 1 / tau
@@ -105,11 +120,10 @@ __device__ __forceinline__ void moments_get_or(Fget&& fget, double& rho, double&
     if (rep_vx(k) != 0) Jx += (long long)rep_vx(k) * M;
     if (rep_vy(k) != 0) Jy += (long long)rep_vy(k) * M;
   }
-  constexpr double S = 1.0 / 4503599627370496.0;  // 2^-52
-  rho = (double)R * S;
-  e = (double)Ei * S;
-  jx = (double)Jx * S;
-  jy = (double)Jy * S;
+  rho = pow2_scale((double)R, -DFIX);  // the fixed-point sums are their values times 2^52
+  e = pow2_scale((double)Ei, -DFIX);
+  jx = pow2_scale((double)Jx, -DFIX);
+  jy = pow2_scale((double)Jy, -DFIX);
   // outside the fixed-point sums' range (see kFixSumMaxExp): plain float64 sums, which
   // also carry infinities and NaNs into the moments as any float64 sum would
   if (emax > kFixSumMaxExp) wide(rho, jx, jy, e);
@@ -142,12 +156,13 @@ __device__ __forceinline__ HermiteA hermite_a(double t, double U) {
   const double tU = t * U, t2 = t * t;
   HermiteA h;
   h.a00 = fma(0.125, U * U, fma(-0.5, U, 1.0) - t) + (tU + t2);
-  h.a01 = fma(-0.25, tU, 0.5 * t) - t2;
-  h.a02 = 0.125 * t2;
-  h.a10 = fma(-0.5, U, 1.0) - 2.0 * t;
-  h.a11 = 0.5 * t;
+  const double t_half = pow2_scale(t, -1);  // t / 2, exactly
+  h.a01 = fma(-0.25, tU, t_half) - t2;
+  h.a02 = pow2_scale(t2, -3);
+  h.a10 = fma(-0.5, U, 1.0) - pow2_scale(t, 1);
+  h.a11 = t_half;
   h.a20 = fma(-0.25, U, 0.5) - 1.5 * t;
-  h.a21 = 0.25 * t;
+  h.a21 = pow2_scale(t, -2);
   return h;
 }
 
@@ -160,7 +175,7 @@ __device__ __forceinline__ void shell_coefficient(const HermiteA& h, double R, i
   K1 = W * fma(h.a11, q, h.a10);
   K2 = W * fma(h.a21, q, h.a20);
   K3 = W * (1.0 / 6.0);
-  K4 = W * (1.0 / 24.0);
+  K4 = pow2_scale(K3, -2);  // W / 24: the double nearest 1/24 is that nearest 1/6 over 4
 }
 
 __device__ __forceinline__ void shell_coefficients(double R, double t, double U, ShellCoef& k) {
@@ -176,8 +191,8 @@ struct Multiples {
 };
 __device__ __forceinline__ Multiples make_multiples(double Ux, double Uy) {
   Multiples m;
-  m.X[0] = 0.0; m.X[1] = Ux; m.X[2] = Ux + Ux; m.X[3] = m.X[2] + Ux;
-  m.Y[0] = 0.0; m.Y[1] = Uy; m.Y[2] = Uy + Uy; m.Y[3] = m.Y[2] + Uy;
+  m.X[0] = 0.0; m.X[1] = Ux; m.X[2] = pow2_scale(Ux, 1); m.X[3] = m.X[2] + Ux;
+  m.Y[0] = 0.0; m.Y[1] = Uy; m.Y[2] = pow2_scale(Uy, 1); m.Y[3] = m.Y[2] + Uy;
   return m;
 }
 __device__ __forceinline__ double dot_v(const Multiples& m, int vxk, int vyk) {
