@@ -22,6 +22,34 @@
 
 namespace d2q37 {
 
+// X * 2^-k for a signed 64-bit X (X != INT64_MIN) and 0 <= k <= 1000, rounded to nearest
+// even: the value (double)X * 2^-k, formed on the integer pipe (count of leading zeros,
+// shift, round, exponent) instead of the float64 pipe's conversion and product.
+__host__ __device__ __forceinline__ double fix_to_double_rn(long long X, int k) {
+  const unsigned long long s = (unsigned long long)(X >> 63);  // 0 or all ones
+  const unsigned long long A = ((unsigned long long)X ^ s) - s;
+#ifdef __CUDA_ARCH__
+  const int lz = __clzll((long long)A);
+#else
+  const int lz = A ? __builtin_clzll(A) : 64;
+#endif
+  const unsigned long long M = A << (lz & 63);                  // leading one at bit 63
+  const unsigned long long mant = M >> 11;                      // 53 bits with the leading one
+  const unsigned long long rem = M & 0x7FFull;
+  const unsigned long long up = (rem > 0x400ull) | ((rem == 0x400ull) & mant);
+  // (e - 1) << 52 plus the 53-bit significand: its leading one, and a carry out of the
+  // rounding, land in the exponent field
+  const unsigned long long bits = ((unsigned long long)(1085 - lz - k) << 52) + mant + (up & 1ull);
+  const unsigned long long r = A == 0 ? 0ull : bits | (s & 0x8000000000000000ull);
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)r);
+#else
+  double d;
+  __builtin_memcpy(&d, &r, 8);
+  return d;
+#endif
+}
+
 // x * 2^k as an integer addition to x's exponent field: GB300 runs float64 at 1/64 of its
 // float32 rate, and these kernels are bound by that pipe, so the exact scalings by powers
 // of two move to the integer pipe.  The result equals the float64 product bit for bit when
@@ -29,12 +57,24 @@ namespace d2q37 {
 // unchanged, and a result below the normal range becomes a zero of x's sign; neither case
 // arises from a valid state (|k| <= 52 and the values scaled here are far inside the
 // normal range, never near its top).
-__device__ __forceinline__ double pow2_scale(double x, int k) {
+__host__ __device__ __forceinline__ double pow2_scale(double x, int k) {
+#ifdef __CUDA_ARCH__
   const long long b = __double_as_longlong(x);
+#else
+  long long b;
+  __builtin_memcpy(&b, &x, 8);
+#endif
   const int e = (int)((b >> 52) & 0x7ff);
   const long long sign = b & (long long)0x8000000000000000ull;
-  const long long scaled = e + k > 0 ? b + ((long long)k << 52) : sign;
-  return __longlong_as_double(e == 0 || e == 0x7ff ? b : scaled);
+  const long long scaled = e + k > 0 ? b + (long long)((unsigned long long)(long long)k << 52) : sign;
+  const long long r = e == 0 || e == 0x7ff ? b : scaled;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(r);
+#else
+  double d;
+  __builtin_memcpy(&d, &r, 8);
+  return d;
+#endif
 }
 
 struct CollideConst {
@@ -120,10 +160,10 @@ __device__ __forceinline__ void moments_get_or(Fget&& fget, double& rho, double&
     if (rep_vx(k) != 0) Jx += (long long)rep_vx(k) * M;
     if (rep_vy(k) != 0) Jy += (long long)rep_vy(k) * M;
   }
-  rho = pow2_scale((double)R, -DFIX);  // the fixed-point sums are their values times 2^52
-  e = pow2_scale((double)Ei, -DFIX);
-  jx = pow2_scale((double)Jx, -DFIX);
-  jy = pow2_scale((double)Jy, -DFIX);
+  rho = fix_to_double_rn(R, DFIX);  // the fixed-point sums are their values times 2^52
+  e = fix_to_double_rn(Ei, DFIX);
+  jx = fix_to_double_rn(Jx, DFIX);
+  jy = fix_to_double_rn(Jy, DFIX);
   // outside the fixed-point sums' range (see kFixSumMaxExp): plain float64 sums, which
   // also carry infinities and NaNs into the moments as any float64 sum would
   if (emax > kFixSumMaxExp) wide(rho, jx, jy, e);

@@ -11,6 +11,8 @@
 //   sapx <a decimal> <b decimal>    -> fx_mulhi_approx(a, b)
 //   suapx <a decimal> <b decimal>   -> fx_mulhi_su_approx(a, b)
 //   const                           -> the shell constants, one shell per line
+//   rn <X decimal> <k>              -> fix_to_double_rn(X, k) (hex bits)
+//   p2 <v as hex bits> <k>          -> pow2_scale(v, k) (hex bits)
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
@@ -39,6 +41,24 @@ int main() {
       unsigned long long bits;
       std::memcpy(&bits, &d, 8);
       std::printf("%016llx\n", bits);
+    } else if (!std::strcmp(cmd, "rn")) {
+      long long X;
+      int k;
+      std::scanf("%lld %d", &X, &k);
+      const double d = fix_to_double_rn(X, k);
+      unsigned long long bits;
+      std::memcpy(&bits, &d, 8);
+      std::printf("%llx\n", bits);
+    } else if (!std::strcmp(cmd, "p2")) {
+      unsigned long long vb;
+      int k;
+      std::scanf("%llx %d", &vb, &k);
+      double v;
+      std::memcpy(&v, &vb, 8);
+      const double d = pow2_scale(v, k);
+      unsigned long long bits;
+      std::memcpy(&bits, &d, 8);
+      std::printf("%llx\n", bits);
     } else if (!std::strcmp(cmd, "top")) {
       long long X;
       int k;

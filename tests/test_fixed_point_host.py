@@ -185,3 +185,47 @@ def test_exact_input_conversion_and_its_range(probe):
         assert flag == int(inside), (v, e)
         if inside:
             assert Fraction(q) == Fraction(v) * 2 ** (59 + e), (v, e)
+
+
+def test_fix_to_double_rn_is_the_correctly_rounded_conversion(probe):
+    """fix_to_double_rn(X, k), the float64 step's conversion of its fixed-point moment sums,
+    is (double)X * 2^-k rounded to nearest even: against Python's correctly rounded
+    float(X) scaled by math.ldexp, on random magnitudes, exact ties (odd and even
+    significands), carries into the exponent, zero and the int64 extremes."""
+    import math
+    rng = random.Random(7)
+    xs = [0, 1, -1, 2 ** 52, 2 ** 53 - 1, 2 ** 53 + 1, 2 ** 53 + 3, 2 ** 63 - 1, -(2 ** 63 - 1), -(2 ** 63),
+          2 ** 63 - 2 ** 10, (2 ** 53 - 1) * 2 ** 10 + 2 ** 9]
+    for _ in range(2000):
+        xs.append(rng.getrandbits(rng.randint(1, 63)) * rng.choice([1, -1]))
+        b = rng.randint(54, 63)
+        x = rng.getrandbits(b) | (1 << (b - 1))
+        sh = b - 53
+        xs.append(((x >> sh << sh) | (1 << (sh - 1))) * rng.choice([1, -1]))   # a tie
+    cases = [(x, k) for x in xs for k in (0, 52, 56)]
+    got = probe([f"rn {x} {k}" for x, k in cases])
+    for (x, k), g in zip(cases, got):
+        want = math.ldexp(float(x), -k)
+        assert from_bits(g) == want and (want != 0 or g == "0"), (x, k, g, want)
+
+
+def test_pow2_scale_is_the_exact_product(probe):
+    """pow2_scale(v, k) = v * 2^k bit for bit for normal v and normal results; zeros,
+    subnormals, infinities and NaNs come back unchanged; results below the normal range
+    become zero with v's sign."""
+    import math
+    rng = random.Random(8)
+    vs = [rng.uniform(-3.0, 3.0) * 10.0 ** rng.randint(-30, 30) for _ in range(3000)]
+    cases = [(v, k) for v in vs for k in (-52, -3, -2, -1, 1)]
+    got = probe([f"p2 {bits(v)} {k}" for v, k in cases])
+    for (v, k), g in zip(cases, got):
+        assert from_bits(g) == math.ldexp(v, k), (v, k, g)
+    special = [0.0, -0.0, 5e-324, -1e-310, float("inf"), float("-inf")]
+    got = probe([f"p2 {bits(v)} -2" for v in special])
+    for v, g in zip(special, got):
+        assert g == bits(v), (v, g)
+    nan = probe([f"p2 {bits(float('nan'))} 3"])[0]
+    assert math.isnan(from_bits(nan))
+    tiny = 2.0 ** -1020
+    assert from_bits(probe([f"p2 {bits(tiny)} -5"])[0]) == 0.0
+    assert probe([f"p2 {bits(-tiny)} -5"])[0] == bits(-0.0)
