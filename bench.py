@@ -59,13 +59,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # no capture of the current kernel exists.  Reads equal the algorithmic bytes; writes read
 # a little low on the captured cases because their tail is still in L2 when the kernel ends.
 TRAFFIC_BYTES_PER_SITE = {
-    "fused": None,         # k_step_fp64 changed since its last capture
-    "fp64fix": 569.2,      # k_step_fix64, 1024 x 2048
+    "fused": 540.6,        # k_step_fp64, 512 x 2048
+    "fp64fix": 569.7,      # k_step_fix64, 1024 x 2048
     "fp32": 272.8,         # k_step_fp32 (shifted), 1024 x 2048
     "fp32c": 273.3,        # k_step_fp32 (conserved moments), 1024 x 2048
-    "adjoint": 830.3,      # k_adj_collide, 512 x 1024 (the adjoint workload's own lattice)
+    "adjoint": 828.3,      # k_adj_collide, 512 x 1024 (the adjoint workload's own lattice)
     "batch_fp32": 259.4,   # k_batch_step<fp32>, 64 small lattices
-    "batch_fp64": 587.2,   # k_batch_step<double>, 8 lattices Lx 128..1024
+    "batch_fp64": 587.0,   # k_batch_step<double>, 8 lattices Lx 128..1024
     "separate": None,
 }
 
