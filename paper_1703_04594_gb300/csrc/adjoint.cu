@@ -32,6 +32,8 @@
 
 namespace d2q37 {
 
+static_assert(D == 2.0, "nu_E = g_t / D is formed as an exact halving");
+
 namespace {
 
 // Vector-Jacobian product of the equilibrium f^eq_i = w_i rho P_i(s_i, U, t),
@@ -253,8 +255,9 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
         VjpSums V;
         if (eq_vjp_sums_fix(usx, usy, t, mu, V)) {
           gr = V.Gr;
-          gux = fma(C, V.Ax, 2.0 * usx * V.Wu);
-          guy = fma(C, V.Ay, 2.0 * usy * V.Wu);
+          const double Wu2 = pow2_scale(V.Wu, 1);  // 2 Wu, exactly
+          gux = fma(C, V.Ax, usx * Wu2);
+          guy = fma(C, V.Ay, usy * Wu2);
           gt = V.Gt;
         } else {
           const EqVjp G = eq_vjp_float64(1.0, usx, usy, t, sf);
@@ -266,9 +269,10 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MIN_BLOCKS) k_adj_collide(const d
       }
       // nu = (d f^eq / d(rho, J, E))^T mu through u = J / rho, T = (E / rho - |u|^2) / D:
       // the factors rho of G and 1 / rho of the chain rule cancel, and E / rho = D T + |u|^2
-      const double nuE = gt * (1.0 / D);
-      const double nuJx = fma(-2.0 * ux, nuE, gux);
-      const double nuJy = fma(-2.0 * uy, nuE, guy);
+      const double nuE = pow2_scale(gt, -1);      // gt / D, D = 2 (exact scalings on the integer pipe)
+      const double m2nuE = pow2_scale(-nuE, 1);   // -2 nuE
+      const double nuJx = fma(ux, m2nuE, gux);
+      const double nuJy = fma(uy, m2nuE, guy);
       const double nuR = fma(nuE, uu - TD, gr - fma(gux, ux, guy * uy));
       // out_i(z) is lambda_i(z - v_i) of the previous step (the transposed pull), or the
       // wall slot of its source column when z - v_i is a ghost

@@ -169,11 +169,12 @@ __device__ __forceinline__ bool eq_vjp_sums_fix(double usx, double usy, double t
   Gt += 4;
   // mu' P / 32 with mu' = mu 2^kmu: the sums are their values times 2^(kmu - 5)
   const int k = kmu - 5;
-  out.Gr = fx_to_double_dp(Gr, k);
-  out.Ax = fx_to_double_dp(Ax, k);
-  out.Ay = fx_to_double_dp(Ay, k);
-  out.Wu = fx_to_double_dp(Wu, k);
-  out.Gt = fx_to_double_dp(Gt, k);
+  // -826 < k <= 974: on the integer pipe, rounded to nearest even
+  out.Gr = fix_to_double_rn(Gr, k);
+  out.Ax = fix_to_double_rn(Ax, k);
+  out.Ay = fix_to_double_rn(Ay, k);
+  out.Wu = fix_to_double_rn(Wu, k);
+  out.Gt = fix_to_double_rn(Gt, k);
   return true;
 }
 

@@ -22,9 +22,10 @@
 
 namespace d2q37 {
 
-// X * 2^-k for a signed 64-bit X (X != INT64_MIN) and 0 <= k <= 1000, rounded to nearest
-// even: the value (double)X * 2^-k, formed on the integer pipe (count of leading zeros,
-// shift, round, exponent) instead of the float64 pipe's conversion and product.
+// X * 2^-k for a signed 64-bit X and -960 <= k <= 1022 (the result is then normal for
+// every X != 0), rounded to nearest even: the value (double)X * 2^-k, formed on the integer
+// pipe (count of leading zeros, shift, round, exponent) instead of the float64 pipe's
+// conversion and product.
 __host__ __device__ __forceinline__ double fix_to_double_rn(long long X, int k) {
   const unsigned long long s = (unsigned long long)(X >> 63);  // 0 or all ones
   const unsigned long long A = ((unsigned long long)X ^ s) - s;
@@ -244,6 +245,9 @@ __device__ __forceinline__ double dot_v(const Multiples& m, int vxk, int vyk) {
 
 // Relaxation: out_i = om1 * f_i + R w_i P_i(s_i), for a whole site.  With om1 = 0 and
 // R = rho this is the plain equilibrium.  `store(i, value)` receives each population.
+// Per opposite pair: E = K0 + s^2 (K2 + s^2 K4), O = s R1 with R1 = K1 + s^2 K3, and
+// E +- O = fma(+-s, R1, E), so the odd part costs no product of its own (8 FP64
+// operations per pair).
 template <class Fget, class Store>
 __device__ __forceinline__ void relax_site_get(Fget&& fget, double om1, double R, double Ux, double Uy, double t,
                                                Store&& store) {
@@ -258,9 +262,9 @@ __device__ __forceinline__ void relax_site_get(Fget&& fget, double om1, double R
     const double s = dot_v(m, rep_vx(j), rep_vy(j));
     const double s2 = s * s;
     const double E = fma(fma(k.K4[sh], s2, k.K2[sh]), s2, k.K0[sh]);
-    const double O = s * fma(k.K3[sh], s2, k.K1[sh]);
-    store(j, fma(om1, fget(j), E + O));
-    store(j + NPAIR, fma(om1, fget(j + NPAIR), E - O));
+    const double R1 = fma(k.K3[sh], s2, k.K1[sh]);  // O = s R1, folded into E +- O
+    store(j, fma(om1, fget(j), fma(s, R1, E)));
+    store(j + NPAIR, fma(om1, fget(j + NPAIR), fma(-s, R1, E)));
   }
 }
 

@@ -191,7 +191,9 @@ def test_fix_to_double_rn_is_the_correctly_rounded_conversion(probe):
     """fix_to_double_rn(X, k), the float64 step's conversion of its fixed-point moment sums,
     is (double)X * 2^-k rounded to nearest even: against Python's correctly rounded
     float(X) scaled by math.ldexp, on random magnitudes, exact ties (odd and even
-    significands), carries into the exponent, zero and the int64 extremes."""
+    significands), carries into the exponent, zero and the int64 extremes, for the
+    scales the kernels use (52 for the moment sums, -825 .. 974 for the adjoint's block
+    fixed point)."""
     import math
     rng = random.Random(7)
     xs = [0, 1, -1, 2 ** 52, 2 ** 53 - 1, 2 ** 53 + 1, 2 ** 53 + 3, 2 ** 63 - 1, -(2 ** 63 - 1), -(2 ** 63),
@@ -202,7 +204,7 @@ def test_fix_to_double_rn_is_the_correctly_rounded_conversion(probe):
         x = rng.getrandbits(b) | (1 << (b - 1))
         sh = b - 53
         xs.append(((x >> sh << sh) | (1 << (sh - 1))) * rng.choice([1, -1]))   # a tie
-    cases = [(x, k) for x in xs for k in (0, 52, 56)]
+    cases = [(x, k) for x in xs for k in (0, 52, 56, -825, 974)]
     got = probe([f"rn {x} {k}" for x, k in cases])
     for (x, k), g in zip(cases, got):
         want = math.ldexp(float(x), -k)
