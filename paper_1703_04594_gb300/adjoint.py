@@ -11,7 +11,7 @@ respect to interface-mode amplitudes.
 The forward steps run in the precision of ``params``: FP64, or FP64 with the fixed-point
 relaxation (LBM_FP64_FIXED, the same states within rounding), so the energy is that of the
 plain forward run bit for bit; the recomputation runs in ``recompute_precision``, by
-default the fixed-point relaxation (3.1x faster on GB300 than the float64 step): the
+default the fixed-point relaxation (2.8x faster on GB300 than the float64 step): the
 recomputed states are only the points the adjoint linearises at, and they agree with the
 forward pass's to float64 rounding (the gradient agrees with a float64 recomputation's
 to ~1e-12).  ``recompute_precision=LBM_FP64`` recomputes with the float64 step; the
