@@ -158,6 +158,20 @@ def test_moments_and_kinetic_energy_match_oracle():
     assert abs(ke - oke) <= 1e-10 * oke
 
 
+def test_kinetic_energy_of_a_drifting_state_matches_oracle():
+    """The kinetic energy against the oracle at the population bar, 1e-12: on a state with a
+    drift (u ~ 0.02) its relative error is that of the moments, not that of velocities near
+    zero (the test above, 4 steps from rest, where 1e-10 is the bound)."""
+    p = lbm.Params(64, 128)
+    rho, ux, uy, T = rt_fields(p, seed=9)
+    fields = (rho, ux + 0.02, uy - 0.01, T)
+    res = lbm.run(p, device_init(p, fields), lbm.empty_state(p), 4)
+    want_f = OL.run(OL.init_equilibrium(*fields), oracle_params(p), 4)
+    ke = float(lbm.kinetic_energy(p, res))
+    oke = float(OL.kinetic_energy(want_f))
+    assert abs(ke - oke) <= 1e-12 * oke, (ke, oke)
+
+
 def test_simulate_host_end_to_end():
     p = lbm.Params(32, 64)
     fields = rt_fields(p, seed=10)
