@@ -226,6 +226,17 @@ def oracle_sample(steps: int, cols: int = 16, threads: int | None = None):
                       f"{dt:.1f} s"}
 
 
+def headline_config(lx: int, ly: int, variant: str, precision: str, world: int) -> dict:
+    """The `config` of the single-lattice line (both arms report the same one)."""
+    name = {"fp32": "FP32-shifted", "fp32c": "FP32-conserved", "fp64fix": "FP64 fixed-point-relax"}.get(precision,
+                                                                                                      "FP64")
+    return {"workload": f"D2Q37 {name} {variant} step, {lx}x{ly} Rayleigh-Taylor lattice",
+            "lx": lx, "ly": ly, "tau": TAU, "gy": GY, "t_bottom": T_BOTTOM, "t_top": T_TOP,
+            "seed": SEED, "variant": variant, "precision": precision,
+            "l2": "state buffers >= 4.9 GB >> 129 MB L2; no flush needed",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(a):
     world, rank, _ = _dist()
     if rank != 0:
@@ -236,8 +247,7 @@ def run_reference(a):
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 16 * LY / cb["value"] / 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"D2Q37 FP64 step, {LX}x{LY} RT lattice (oracle on a bounded crop)",
-                       "lx": LX, "ly": LY, "tau": TAU, "gy": GY},
+            "config": headline_config(LX, LY, "fused", "fp64", a.gpus),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -426,14 +436,7 @@ def run_ours(a):
                 "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+i64+f64" if fp32 else ("f64+i64" if fix else "f64"),
                 "data": "synthetic",
-                "config": {"workload": f"D2Q37 {'FP32-shifted' if fp32 else ('FP64 fixed-point-relax' if fix else 'FP64')} "
-                                       f"{a.variant} step, "
-                                       f"{lx}x{ly} Rayleigh-Taylor lattice",
-                           "lx": lx, "ly": ly, "tau": TAU, "gy": GY, "t_bottom": T_BOTTOM, "t_top": T_TOP,
-                           "seed": SEED, "variant": a.variant,
-                           "precision": a.precision,
-                           "l2": "state buffers >= 4.9 GB >> 129 MB L2; no flush needed",
-                           "parallelism": f"replicas x{world}"},
+                "config": headline_config(lx, ly, a.variant, a.precision, world),
                 "roofline": roofline, "e2e": e2e,
                 **({"propagate_kernel": prop_line} if prop_line else {}),
                 **({"fp64_fixed_relax": fixed_line} if fixed_line else {}),
