@@ -50,7 +50,8 @@ enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, L
 /* LBM_FP64: float64 populations, float64 collision arithmetic (moment sums in exact 64-bit
  * fixed point for sites whose populations are all below 8 in magnitude, plain float64 sums
  * for any other site, so every finite state is handled; a non-finite population makes its
- * site's outputs NaN).  LBM_FP32_SHIFTED: float32 storage of g_i = f_i - w_i rho0, for
+ * site's outputs NaN; the sums' conversion and the products by powers of two run on the
+ * integer pipe, with the bits of their float64 counterparts).  LBM_FP32_SHIFTED: float32 storage of g_i = f_i - w_i rho0, for
  * states with every |g_i| < 8 (choose rho0 near the state's density); a site holding a
  * larger deviation, an infinity or a NaN gets NaN moments, and every population it
  * produces is NaN.  LBM_FP64_FIXED:
@@ -61,11 +62,12 @@ enum lbm_status { LBM_OK = 0, LBM_EINVAL = 1, LBM_ECUDA = 2, LBM_ETIMEOUT = 3, L
  * lbm_kinetic_energy*, lbm_simulate_host and the batch entry points accept it; the separate
  * kernels, layouts and adjoint entry points take LBM_FP64 (its states are the same). */
 /* LBM_FP32_CONSERVED: the FP32_SHIFTED storage (same buffers, interchangeable states) with a
- * collision that restores the exact post-collision mass and energy of every site after its
- * float32 arithmetic (a second moment sum over the outputs and a correction along the even
- * first Hermite polynomials): float32 rounding then no longer accumulates as pressure noise
- * in the conserved fields, which is what limits the velocity accuracy of long FP32_SHIFTED
- * runs.  Accepted wherever LBM_FP32_SHIFTED is. */
+ * collision that restores the exact post-collision mass, momentum and energy of every site
+ * after its float32 arithmetic (a second, exact moment sum over the outputs and a correction
+ * along w_i (alpha + beta . v_i + gamma (|v_i|^2 - m)), the first Hermite polynomials over all
+ * 37 populations): float32 rounding then no longer accumulates in the conserved fields,
+ * which is what limits the velocity accuracy of long FP32_SHIFTED runs.  Accepted wherever
+ * LBM_FP32_SHIFTED is. */
 enum lbm_precision { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP64_FIXED = 2, LBM_FP32_CONSERVED = 3 };
 enum lbm_bc { LBM_BC_WALLS = 0, LBM_BC_PERIODIC_Y = 1 /* test mode: y wraps like x */ };
 
