@@ -340,20 +340,26 @@ __device__ __forceinline__ void reduce_add_256(const double* __restrict__ part, 
 // Step 2: the wall rows' share of the transposed bc, after step 1 has written every
 // lambda entry: lambda_j(x, 0) += sum over the bottom slots of column x of the slot's value
 // times its ghost's weight w_i P_i(T_bottom), for all j (the ghost values' dependence on
-// rho_w(x) = sum_j f_j(x, 0)), and likewise for row ly - 1.  One thread per column and
-// wall (blockIdx.y: 0 bottom, 1 top); block (0, 2) adds the step's dL/dtau partials to
-// *dtau (the reduction needs step 1 complete too, so it shares this launch).
+// rho_w(x) = sum_j f_j(x, 0)), and likewise for row ly - 1.  One thread per column, wall and
+// population j: each forms its column's wall sum in the same fixed order (so the 37 entries
+// of a column receive the same value; the column's 26 slots are read from cache) and adds
+// it to its own entry, so the launch spreads over the GPU instead of running 37 dependent
+// updates per column on a few blocks.  The grid's last block adds the step's dL/dtau
+// partials to *dtau (the reduction needs step 1 complete too, so it shares this launch).
 __global__ void __launch_bounds__(256) k_adj_walls(const double* __restrict__ side, double* __restrict__ lam,
                                                    StepArgs a, const double* __restrict__ part, long long n_part,
                                                    double* dtau) {
-  if (blockIdx.y == 2) {
-    if (blockIdx.x == 0) reduce_add_256(part, n_part, dtau);
+  if (blockIdx.x == gridDim.x - 1) {  // uniform per block
+    reduce_add_256(part, n_part, dtau);
     return;
   }
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= a.lx) return;
-  const int top = blockIdx.y;
-  const double* src = side + ((long long)top * a.lx + x) * kGhostSlots;
+  const long long item = (long long)blockIdx.x * 256 + threadIdx.x;  // (top * lx + x) * Q + j
+  if (item >= 2LL * a.lx * Q) return;
+  const int j = (int)(item % Q);
+  const long long col = item / Q;  // top * lx + x: the slot column of `side`
+  const int top = (int)(col / a.lx);
+  const int x = (int)(col - (long long)top * a.lx);
+  const double* src = side + col * kGhostSlots;
   double wall = 0.0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {  // rows in increasing y, then the ghost's weight
@@ -366,9 +372,7 @@ __global__ void __launch_bounds__(256) k_adj_walls(const double* __restrict__ si
       wall = vy(i) > 0 ? fma(t, a.wall_b[i], wall) : wall;
     }
   }
-  double* dst = lam + (long long)x * a.pitch + (top ? a.ly - 1 : 0);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) dst[i * a.pop] += wall;
+  lam[j * a.pop + (long long)x * a.pitch + (top ? a.ly - 1 : 0)] += wall;
 }
 
 // Adds sum(part[0..n)) to *acc in a fixed order (one block of 256 threads).
@@ -441,7 +445,9 @@ cudaError_t launch_adjoint_step(const double* fin, const double* lam_next, doubl
     k_adj_collide<true><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, k);
   } else {
     k_adj_collide<false><<<site_grid(a), blk, 0, s>>>(fin, lam_next, lam, side, part, a, k);
-    k_adj_walls<<<dim3((a.lx + 255) / 256, 3), 256, 0, s>>>(side, lam, a, part, adjoint_partial_count(a), dtau);
+    const long long items = 2LL * a.lx * Q;  // (column, wall, population), plus one block for the dtau sum
+    k_adj_walls<<<(unsigned)((items + 255) / 256) + 1, 256, 0, s>>>(side, lam, a, part, adjoint_partial_count(a),
+                                                                    dtau);
     return cudaGetLastError();
   }
   k_reduce_add<<<1, 256, 0, s>>>(part, adjoint_partial_count(a), dtau);
